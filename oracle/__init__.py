@@ -1,0 +1,188 @@
+"""CPU FP64 oracle for the COSMOS evolution problem — test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+leg of ``bench.py`` may import this package.  The product package
+(``paper_2606_02053_gb300``) never imports it and shares no code with it.
+
+The arithmetic lives in ``cosmos_oracle.cpp`` (plain C++17, FP64, compiled
+with ``-ffp-contract=off``).  This module compiles it with g++ on first use,
+loads it with ctypes and exposes numpy-level wrappers.  Arrays follow the
+oracle's own layout: ``state[f, k, j, i]`` (i fastest), C-contiguous float64.
+
+Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
+  rhs / rhs_points / rk4_step : flat space, Fourier symbols, translation and
+      axis permutation, gauge-wave closed form + 4th-order convergence, ADM
+      cross-check against an autodiff evaluation of the Einstein equations
+      (vacuum, fluid, scalar), homogeneous FLRW expansion law.
+  constraints : autodiff ADM constraints (4th-order convergence), gauge wave.
+  init        : gauge-wave closed form; FLRW + zeta gives H = 0 (discrete).
+  flop_count  : counts only; no physics.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cosmos_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CXXFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (g++); returns its path."""
+    with _lock:
+        stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+        if force or stale:
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["g++", *CXXFLAGS, "-o", tmp, _SRC])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_L = ctypes.POINTER(ctypes.c_long)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        L.oracle_nfields.argtypes = [_D]
+        L.oracle_nfields.restype = ctypes.c_int
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_max_threads.restype = ctypes.c_int
+        L.oracle_rhs.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
+        L.oracle_rhs_points.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, ctypes.c_long, _L, _D]
+        L.oracle_rhs_planes.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, ctypes.c_long, ctypes.c_long, _D]
+        L.oracle_rk4_step.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double]
+        L.oracle_constraints.argtypes = [_I, _D, _D, _D, _D, _D, _D]
+        L.oracle_init.argtypes = [_I, _D, _D, _D, _D, _D]
+        L.oracle_flop_count.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
+        _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# Parameter containers (plain data)
+# --------------------------------------------------------------------------
+class OGrid:
+    """Uniform periodic grid: n = (nx, ny, nz), spacing h, coordinate x0 of point 0."""
+
+    def __init__(self, n, h, x0=(0.0, 0.0, 0.0)):
+        self.n = tuple(int(v) for v in n)
+        self.h = tuple(float(v) for v in (h if np.ndim(h) else (h, h, h)))
+        self.x0 = tuple(float(v) for v in x0)
+
+    @property
+    def npts(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def c(self):
+        return ((ctypes.c_int * 3)(*self.n), (ctypes.c_double * 3)(*self.h), (ctypes.c_double * 3)(*self.x0))
+
+
+def params_array(slicing=0, shift=1, eta=2.0, ko_sigma=0.1, w=1.0 / 3.0, fluid=0, scalar=0, H0=0.0, t0=0.0):
+    return np.array([slicing, shift, eta, ko_sigma, w, fluid, scalar, H0, t0], dtype=np.float64)
+
+
+def nfields(params) -> int:
+    return 24 + 4 * int(params[5]) + 2 * int(params[6])
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _check_state(g: OGrid, params, state):
+    nf = nfields(params)
+    assert state.dtype == np.float64 and state.flags.c_contiguous
+    assert state.shape == (nf, g.n[2], g.n[1], g.n[0]), (state.shape, nf, g.n)
+
+
+def set_threads(n: int):
+    lib().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+def rhs(g: OGrid, params, state, t=0.0):
+    _check_state(g, params, state)
+    out = np.empty_like(state)
+    n, h, x0 = g.c()
+    lib().oracle_rhs(n, h, x0, _dp(params), _dp(state), float(t), _dp(out))
+    return out
+
+
+def rhs_points(g: OGrid, params, state, pts, t=0.0):
+    """RHS at (i, j, k) points; returns array [npts, nf]."""
+    _check_state(g, params, state)
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.int64).reshape(-1, 3))
+    out = np.empty((pts.shape[0], nfields(params)), dtype=np.float64)
+    n, h, x0 = g.c()
+    lib().oracle_rhs_points(n, h, x0, _dp(params), _dp(state), float(t), pts.shape[0],
+                            pts.ctypes.data_as(_L), _dp(out))
+    return out
+
+
+def rhs_planes(g: OGrid, params, state, k0, k1, t=0.0):
+    _check_state(g, params, state)
+    out = np.empty((nfields(params), k1 - k0, g.n[1], g.n[0]), dtype=np.float64)
+    n, h, x0 = g.c()
+    lib().oracle_rhs_planes(n, h, x0, _dp(params), _dp(state), float(t), int(k0), int(k1), _dp(out))
+    return out
+
+
+def rk4_step(g: OGrid, params, state, t, dt):
+    """In place: state <- RK4 step of size dt from time t."""
+    _check_state(g, params, state)
+    n, h, x0 = g.c()
+    lib().oracle_rk4_step(n, h, x0, _dp(params), _dp(state), float(t), float(dt))
+    return state
+
+
+def evolve(g: OGrid, params, state, t, dt, steps):
+    for s in range(steps):
+        rk4_step(g, params, state, t + s * dt, dt)
+    return state
+
+
+def constraints(g: OGrid, params, state):
+    """Returns (ham_mom[4, nz, ny, nx], norms[8])."""
+    _check_state(g, params, state)
+    hm = np.empty((4, g.n[2], g.n[1], g.n[0]), dtype=np.float64)
+    norms = np.empty(8, dtype=np.float64)
+    n, h, x0 = g.c()
+    lib().oracle_constraints(n, h, x0, _dp(params), _dp(state), _dp(hm), _dp(norms))
+    return hm, norms
+
+
+def id_array(kind, A=0.0, mu=0.0, sigma=0.125, q=(1.0, 1.0, 1.0), center=(0.0, 0.0, 0.0), a0=1.0, t=0.0):
+    return np.array([kind, A, mu, sigma, *q, *center, a0, t], dtype=np.float64)
+
+
+def init(g: OGrid, params, idarr):
+    state = np.empty((nfields(params), g.n[2], g.n[1], g.n[0]), dtype=np.float64)
+    n, h, x0 = g.c()
+    lib().oracle_init(n, h, x0, _dp(params), _dp(np.asarray(idarr, dtype=np.float64)), _dp(state))
+    return state
+
+
+def flop_count(g: OGrid, params, state, t=0.0):
+    """{add, mul, div, sqrt, cmp} of one RHS evaluation at one point."""
+    _check_state(g, params, state)
+    c = np.empty(5, dtype=np.float64)
+    n, h, x0 = g.c()
+    lib().oracle_flop_count(n, h, x0, _dp(params), _dp(state), float(t), _dp(c))
+    return dict(zip(["add", "mul", "div", "sqrt", "cmp"], c.tolist()))
