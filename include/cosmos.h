@@ -1,0 +1,170 @@
+/*
+ * cosmos.h -- C ABI of libcosmos_gb300.so: BSSN + perfect-fluid + massless-
+ * scalar evolution on a periodic 3D grid, FP64, on one NVIDIA GB300 GPU.
+ *
+ * The calls follow the evolution problem of Yoo et al., "COSMOS: a numerical
+ * relativity code specialized for PBH formation" (section "Physical system
+ * settings"): the Einstein equations G = 8 pi T with T = T^SC + T^FL,
+ * T^FL = (rho + P) u u + P g, P = w rho, box phi = 0 and div T^FL = 0,
+ * integrated in the 3+1 (BSSN, chi-variant) form that the paper refers to
+ * the standard textbooks for, from long-wavelength initial data whose fluid
+ * density satisfies the Hamiltonian constraint (same section, last
+ * paragraph); the fluid uses the Kurganov-Tadmor central scheme the paper
+ * names.  Spatial derivatives are 4th-order centred finite differences with
+ * 6th-derivative Kreiss-Oliger dissipation; time integration is classic RK4.
+ *
+ * Conventions (all calls):
+ *  - Units G = c = 1.  Grid points x = x0 + (i, j, k) * h, periodic.
+ *  - State layout: structure of arrays, double precision.  Field f of point
+ *    (i, j, k) is state[f * fstride + (k * ny + j) * pitch + i] with
+ *    fstride = pitch * ny * nz (cosmos_field_stride).  Field order:
+ *      0 chi, 1..6 gt_xx gt_xy gt_xz gt_yy gt_yz gt_zz, 7 K,
+ *      8..13 At_xx..At_zz, 14..16 Gt^x Gt^y Gt^z, 17 alpha,
+ *      18..20 beta^x..z, 21..23 B^x..z,
+ *      then (fluid on) 24 tau~ = sqrt(gamma) E, 25..27 S~_i = sqrt(gamma) J_i,
+ *      then (scalar on) phi, Pi  (Pi = -n^mu d_mu phi).
+ *    Padding columns i in [nx, pitch) are never read or written.
+ *  - Memory: every pointer named state/rhs/ws/... is DEVICE memory owned by
+ *    the caller (e.g. a torch CUDA tensor), 16-byte aligned.  The library
+ *    allocates no device memory in any call.  Work buffers are passed as
+ *    (ws, ws_bytes); cosmos_workspace_bytes gives the size each op needs.
+ *  - stream: a cudaStream_t passed as void*; NULL = legacy default stream.
+ *    Calls are asynchronous on that stream unless stated otherwise.
+ *  - Return value: COSMOS_OK (0) or a negative error code; no call throws.
+ *    Arguments are validated before any launch; on error nothing is
+ *    launched.  COSMOS_ECUDA reports a failed CUDA launch or copy
+ *    (cosmos_last_cuda_error gives the cudaError_t value).
+ */
+#ifndef COSMOS_GB300_H
+#define COSMOS_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COSMOS_OK 0
+#define COSMOS_EINVAL (-1)      /* bad argument (sizes, NULL pointer, option) */
+#define COSMOS_ECUDA (-2)       /* CUDA runtime error */
+#define COSMOS_EWORKSPACE (-3)  /* workspace smaller than cosmos_workspace_bytes */
+#define COSMOS_EALIGN (-4)      /* pointer not 16-byte aligned */
+#define COSMOS_ENONFINITE (-5)  /* NaN/Inf or unphysical fluid state detected */
+
+/* Workspace ops for cosmos_workspace_bytes */
+#define COSMOS_OP_RHS 0
+#define COSMOS_OP_RK4 1
+#define COSMOS_OP_CONSTRAINTS 2
+#define COSMOS_OP_INIT 3
+
+typedef struct {
+  int nx, ny, nz; /* grid points per direction, each >= 1 */
+  int pitch;      /* doubles between rows (>= nx) */
+  double h[3];    /* grid spacing per direction (> 0) */
+  double x0[3];   /* coordinates of point (0, 0, 0) */
+} cosmos_grid;
+
+typedef struct {
+  int slicing;     /* 0: 1+log  d_t alpha = beta.d alpha - 2 alpha (K - K_ref(t));
+                      1: harmonic d_t alpha = beta.d alpha - alpha^2 (K - K_ref(t)) */
+  int shift;       /* 0: frozen shift (d_t beta = d_t B = 0); 1: Gamma-driver
+                      d_t beta = beta.d beta + 3/4 B,
+                      d_t B = beta.d B + d_t Gt - beta.d Gt - eta B */
+  int fluid;       /* 1: perfect fluid P = w rho (4 extra fields) */
+  int scalar;      /* 1: massless scalar field (2 extra fields) */
+  double eta;      /* Gamma-driver damping */
+  double ko_sigma; /* Kreiss-Oliger strength sigma (>= 0) */
+  double w;        /* equation of state P = w rho, 0 < w <= 1 when fluid on */
+  double H0, t0;   /* background: K_ref(t) = -3 H0 / (1 + 3/2 (1 + w) H0 (t - t0));
+                      H0 = 0 gives K_ref = 0 */
+} cosmos_params;
+
+typedef struct {
+  int kind;       /* 0: gauge wave  ds^2 = -H dt^2 + H dx^2 + dy^2 + dz^2,
+                        H = 1 - A sin(2 pi (x - t)/(nx h_x)), at time t;
+                     1: FLRW + curvature perturbation zeta at leading
+                        gradient order: gamma_ij = a0^2 e^{2 zeta} delta_ij,
+                        K = -3 H0, At = 0, alpha = 1, beta = B = 0, fluid at
+                        rest with E fixed by the discrete Hamiltonian
+                        constraint (requires fluid on);
+                        zeta = mu exp(-r_e^2 / (2 sigma^2)),
+                        r_e^2 = sum_i ((x_i - center_i)/q_i)^2 */
+  double A;
+  double mu, sigma;
+  double q[3];
+  double center[3];
+  double a0;
+  double t;
+} cosmos_id;
+
+/* Number of evolved fields: 24 + 4 fluid + 2 scalar. */
+int cosmos_nfields(const cosmos_params* p);
+
+/* Doubles between consecutive fields: pitch * ny * nz. */
+size_t cosmos_field_stride(const cosmos_grid* g);
+
+/* Bytes of workspace needed by an op (COSMOS_OP_*); 0 if none. */
+size_t cosmos_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int op);
+
+/* Initial data (section "Physical system settings", initial-data paragraph).
+ * Writes every field of `state`.  ws: COSMOS_OP_INIT bytes. */
+int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* Right-hand side d_t U = F(U, t) of every field (BSSN equations, gauge,
+ * matter sources, Kreiss-Oliger dissipation, KT flux divergence), written
+ * to `rhs` (same layout as state).  ws: COSMOS_OP_RHS bytes. */
+int cosmos_rhs(const cosmos_grid* g, const cosmos_params* p, const double* state, double* rhs, double t, void* ws,
+               size_t ws_bytes, void* stream);
+
+/* One fused RK4 stage s in {1, 2, 3, 4} (classic RK4, stage time
+ * t + c_s dt with c = 0, 1/2, 1/2, 1):
+ *   k = F(U_s, t + c_s dt)
+ *   s = 1:  U_next = U_n + dt/2 k,  acc = k
+ *   s = 2:  U_next = U_n + dt/2 k,  acc += 2 k
+ *   s = 3:  U_next = U_n + dt k,    acc += 2 k
+ *   s = 4:  U_n   <- U_n + dt/6 (acc + k)   (U_next unused)
+ * U_s must not alias U_next or acc.  U_s = U_n is allowed (stage 1).
+ * ws: COSMOS_OP_RHS bytes. */
+int cosmos_rk4_stage(const cosmos_grid* g, const cosmos_params* p, int stage, const double* U_s, double* U_n,
+                     double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes, void* stream);
+
+/* One classic RK4 step of size dt from time t, in place on `state`
+ * (four cosmos_rk4_stage launches).  ws: COSMOS_OP_RK4 bytes
+ * (two stage buffers, the accumulator and the fluid buffers). */
+int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* End-to-end step with HOST buffers: copies host_in (pageable or pinned
+ * host memory, cosmos_field_stride * nfields doubles) to dev_state, runs
+ * `steps` RK4 steps and copies the result to host_out; synchronous. */
+int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
+                       double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream);
+
+/* Hamiltonian and (conformal) momentum constraints
+ *   H   = R + 2/3 K^2 - At_ij At^ij - 16 pi rho_H
+ *   M^i = gt^ik gt^jl Dt_j At_kl - 3/(2 chi) At^ij d_j chi - 2/3 gt^ij d_j K - 8 pi gt^ij J_j
+ * per point into ham_mom (4 fields in state layout, or NULL) and their norms
+ * into norms_host[8] = {L2(H), L2(Mx), L2(My), L2(Mz), Linf(H), ...},
+ * L2 = sqrt(mean square over all points).  Synchronous (norms on the host).
+ * ws: COSMOS_OP_CONSTRAINTS bytes. */
+int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
+                       double norms_host[8], void* ws, size_t ws_bytes, void* stream);
+
+/* Measured FP64 fused-multiply-add throughput of the current device, in
+ * flop/s (2 flop per DFMA), from a timed launch of independent DFMA chains
+ * on every SM.  Synchronous; allocates nothing (writes one double per thread
+ * into `scratch`, which must hold 152 * 8 * 256 doubles). */
+int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream);
+
+/* cudaError_t of the last COSMOS_ECUDA returned by this thread. */
+int cosmos_last_cuda_error(void);
+
+/* Static description of an error code. */
+const char* cosmos_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COSMOS_GB300_H */

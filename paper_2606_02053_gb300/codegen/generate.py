@@ -1,0 +1,115 @@
+"""Write the generated CUDA headers of the pointwise algebra.
+
+Usage: python -m paper_2606_02053_gb300.codegen.generate [--check]
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+from . import bssn
+from . import fluid as fluid_dsl
+from .expr import emit_function, op_counts
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")
+
+VARIANTS = [("vac", False, False), ("fluid", True, False), ("scalar", False, True), ("fluid_scalar", True, True)]
+
+HEADER = """// GENERATED by paper_2606_02053_gb300/codegen/generate.py -- do not edit.
+// Pointwise BSSN + matter right-hand side (without Kreiss-Oliger dissipation
+// and without the fluid flux divergence), one grid point per call.
+// Input layout and parameters: see paper_2606_02053_gb300/codegen/bssn.py.
+#pragma once
+
+struct AlgebraParams {
+  double eta;       // Gamma-driver damping
+  double Kref;      // background trace K_ref at the stage time
+  double lapse_c1;  // d_t alpha = beta.d alpha - alpha (c1 + c2 alpha)(K - Kref)
+  double lapse_c2;
+  double shift_on;  // 1: Gamma-driver shift, 0: frozen shift
+  double w;         // fluid equation of state P = w rho
+};
+"""
+
+
+def render() -> dict:
+    files = {}
+    body = [HEADER]
+    stats = []
+    for name, fluid, scalar in VARIANTS:
+        g, L, out = bssn.algebra(fluid, scalar)
+        c = op_counts(g, out)
+        stats.append((name, c))
+        body.append(f"// variant {name}: fluid={int(fluid)} scalar={int(scalar)}; ops {dict(sorted(c.items()))}")
+        body.append(f"namespace alg_{name} {{")
+        body.append(f"constexpr int NF = {L['nf']};")
+        body.append(f"constexpr int ND1 = {len(L['d1'])};")
+        body.append(f"constexpr int ND2 = {len(L['d2'])};")
+        body.append(f"constexpr int NIN = {L['nin']};")
+        body.append(_table_fn("d1_field", L["d1"]))
+        body.append(_table_fn("d2_field", L["d2"]))
+        body.append(emit_function(g, "rhs", L["names"], out, ["AlgebraParams"]))
+        body.append(emit_function(g, "constraints", L["names"], g.constraints, ["AlgebraParams"]))
+        body.append(f"}}  // namespace alg_{name}\n")
+    files["bssn_algebra.cuh"] = "\n".join(body)
+    fb = [FLUID_HEADER]
+    g, names, out = fluid_dsl.prim()
+    stats.append(("prim", op_counts(g, out)))
+    fb.append("// inputs: " + ", ".join(names))
+    fb.append(emit_function(g, "fluid_prim", names, out, ["FluidParams"]))
+    for d in range(3):
+        g, names, out = fluid_dsl.face_flux(d)
+        stats.append((f"face{d}", op_counts(g, out)))
+        if d == 0:
+            fb.append("// face-flux inputs: " + ", ".join(names))
+        fb.append(emit_function(g, f"fluid_face_flux_{d}", names, out, ["FluidParams"]))
+    files["fluid_algebra.cuh"] = "\n".join(fb)
+    return files, stats
+
+
+def _table_fn(name, values):
+    expr = "-1"
+    for m in reversed(range(len(values))):
+        expr = f"(m == {m} ? {values[m]} : {expr})"
+    return f"__host__ __device__ __forceinline__ constexpr int {name}(int m) {{ return {expr}; }}"
+
+
+FLUID_HEADER = """// GENERATED by paper_2606_02053_gb300/codegen/generate.py -- do not edit.
+// Fluid primitive recovery and Kurganov-Tadmor face fluxes (see
+// paper_2606_02053_gb300/codegen/fluid.py for the formulas and the inputs).
+#pragma once
+
+struct FluidParams {
+  double w;       // P = w rho
+  double sqrt_w;  // sound speed
+};
+"""
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--check", action="store_true", help="fail if the committed files differ")
+    a = ap.parse_args(argv)
+    files, stats = render()
+    os.makedirs(OUT_DIR, exist_ok=True)
+    stale = []
+    for fn, text in files.items():
+        path = os.path.join(OUT_DIR, fn)
+        old = open(path).read() if os.path.exists(path) else None
+        if old != text:
+            stale.append(fn)
+            if not a.check:
+                with open(path, "w") as f:
+                    f.write(text)
+    for name, c in stats:
+        print(name, sum(v for k, v in c.items()), dict(sorted(c.items())))
+    if a.check and stale:
+        print("stale:", stale)
+        return 1
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+"""Thin ctypes binding of libcosmos_gb300.so (declared in include/cosmos.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch CUDA tensors (float64); streams are torch
+CUDA streams.  Functions keep the C names and return the C error code,
+except that ``check`` raises ``CosmosError`` on a non-zero code.
+
+If the shared library is missing this module raises on import of any entry
+point: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcosmos_gb300.so")
+
+COSMOS_OK = 0
+COSMOS_EINVAL = -1
+COSMOS_ECUDA = -2
+COSMOS_EWORKSPACE = -3
+COSMOS_EALIGN = -4
+COSMOS_ENONFINITE = -5
+COSMOS_OP_RHS, COSMOS_OP_RK4, COSMOS_OP_CONSTRAINTS, COSMOS_OP_INIT = 0, 1, 2, 3
+
+
+class cosmos_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("h", ctypes.c_double * 3), ("x0", ctypes.c_double * 3)]
+
+
+class cosmos_params(ctypes.Structure):
+    _fields_ = [("slicing", ctypes.c_int), ("shift", ctypes.c_int), ("fluid", ctypes.c_int), ("scalar", ctypes.c_int),
+                ("eta", ctypes.c_double), ("ko_sigma", ctypes.c_double), ("w", ctypes.c_double),
+                ("H0", ctypes.c_double), ("t0", ctypes.c_double)]
+
+
+class cosmos_id(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("A", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("q", ctypes.c_double * 3), ("center", ctypes.c_double * 3), ("a0", ctypes.c_double),
+                ("t", ctypes.c_double)]
+
+
+class CosmosError(RuntimeError):
+    pass
+
+
+_lib = None
+_P = ctypes.c_void_p
+_G = ctypes.POINTER(cosmos_grid)
+_PP = ctypes.POINTER(cosmos_params)
+_IDP = ctypes.POINTER(cosmos_id)
+_D = ctypes.c_double
+_S = ctypes.c_size_t
+
+_SIGS = {
+    "cosmos_nfields": ([_PP], ctypes.c_int),
+    "cosmos_field_stride": ([_G], ctypes.c_size_t),
+    "cosmos_workspace_bytes": ([_G, _PP, ctypes.c_int], ctypes.c_size_t),
+    "cosmos_init_grid": ([_G, _PP, _IDP, _P, _P, _S, _P], ctypes.c_int),
+    "cosmos_rhs": ([_G, _PP, _P, _P, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_rk4_stage": ([_G, _PP, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_rk4_step": ([_G, _PP, _P, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
+    "cosmos_probe_fp64": ([_P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_last_cuda_error": ([], ctypes.c_int),
+    "cosmos_strerror": ([ctypes.c_int], ctypes.c_char_p),
+}
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise CosmosError(f"{LIB_PATH} is missing: build it with paper_2606_02053_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def check(code: int):
+    if code != COSMOS_OK:
+        msg = lib().cosmos_strerror(code).decode()
+        extra = f" (cudaError {lib().cosmos_last_cuda_error()})" if code == COSMOS_ECUDA else ""
+        raise CosmosError(f"cosmos error {code}: {msg}{extra}")
+    return code
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ws(ws):
+    if ws is None:
+        return None, 0
+    return _ptr(ws), ws.numel() * ws.element_size()
+
+
+# ---- C entry points (same names) ----------------------------------------------
+def cosmos_nfields(p: cosmos_params) -> int:
+    return lib().cosmos_nfields(ctypes.byref(p))
+
+
+def cosmos_field_stride(g: cosmos_grid) -> int:
+    return lib().cosmos_field_stride(ctypes.byref(g))
+
+
+def cosmos_workspace_bytes(g: cosmos_grid, p: cosmos_params, op: int) -> int:
+    return lib().cosmos_workspace_bytes(ctypes.byref(g), ctypes.byref(p), op)
+
+
+def cosmos_init_grid(g, p, ident, state, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_init_grid(ctypes.byref(g), ctypes.byref(p), ctypes.byref(ident), _ptr(state), w, nb,
+                                  _stream(stream))
+
+
+def cosmos_rhs(g, p, state, rhs, t, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_rhs(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(rhs), float(t), w, nb,
+                            _stream(stream))
+
+
+def cosmos_rk4_stage(g, p, stage, U_s, U_n, U_next, acc, t, dt, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_rk4_stage(ctypes.byref(g), ctypes.byref(p), int(stage), _ptr(U_s), _ptr(U_n), _ptr(U_next),
+                                  _ptr(acc), float(t), float(dt), w, nb, _stream(stream))
+
+
+def cosmos_rk4_step(g, p, state, t, dt, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_rk4_step(ctypes.byref(g), ctypes.byref(p), _ptr(state), float(t), float(dt), w, nb,
+                                 _stream(stream))
+
+
+def cosmos_evolve_host(g, p, host_in, host_out, dev_state, steps, t, dt, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_evolve_host(ctypes.byref(g), ctypes.byref(p), _ptr(host_in), _ptr(host_out),
+                                    _ptr(dev_state), int(steps), float(t), float(dt), w, nb, _stream(stream))
+
+
+def cosmos_constraints(g, p, state, ham_mom, norms_out, ws=None, stream=None) -> int:
+    """norms_out: a ctypes double[8] (or anything exposing 8 writable doubles)."""
+    w, nb = _ws(ws)
+    return lib().cosmos_constraints(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(ham_mom), norms_out, w, nb,
+                                    _stream(stream))
+
+
+def cosmos_probe_fp64(scratch, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    check(lib().cosmos_probe_fp64(_ptr(scratch), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+# ---- convenience constructors (plain data) -----------------------------------
+def make_grid(n, h, x0=(0.0, 0.0, 0.0), pitch=None) -> cosmos_grid:
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+    hh = (h, h, h) if isinstance(h, (int, float)) else h
+    g = cosmos_grid()
+    g.nx, g.ny, g.nz = nx, ny, nz
+    g.pitch = nx if pitch is None else pitch
+    g.h[:] = list(hh)
+    g.x0[:] = list(x0)
+    return g
+
+
+def make_params(slicing=0, shift=1, fluid=0, scalar=0, eta=2.0, ko_sigma=0.1, w=1.0 / 3.0, H0=0.0,
+                t0=0.0) -> cosmos_params:
+    p = cosmos_params()
+    p.slicing, p.shift, p.fluid, p.scalar = slicing, shift, fluid, scalar
+    p.eta, p.ko_sigma, p.w, p.H0, p.t0 = eta, ko_sigma, w, H0, t0
+    return p
+
+
+def make_id(kind, A=0.0, mu=0.0, sigma=0.125, q=(1.0, 1.0, 1.0), center=(0.0, 0.0, 0.0), a0=1.0, t=0.0) -> cosmos_id:
+    d = cosmos_id()
+    d.kind, d.A, d.mu, d.sigma = kind, A, mu, sigma
+    d.q[:] = list(q)
+    d.center[:] = list(center)
+    d.a0, d.t = a0, t
+    return d

@@ -1,0 +1,498 @@
+// C ABI of libcosmos_gb300 (declared in include/cosmos.h): argument
+// validation, workspace layout, initial-data and reduction kernels, and the
+// launch sequences of the right-hand side, RK4 and constraint calls.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace cosmos {
+
+static thread_local int g_last_cuda_error = 0;
+
+static int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return COSMOS_ECUDA;
+}
+
+#define CK(expr)                             \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+Coef make_coef(const cosmos_grid* g, double sigma) {
+  Coef c;
+  for (int d = 0; d < 3; ++d) {
+    const double h = g->h[d];
+    c.d1a[d] = 8.0 / (12.0 * h);
+    c.d1b[d] = 1.0 / (12.0 * h);
+    c.d2a[d] = 16.0 / (12.0 * h * h);
+    c.d2b[d] = 1.0 / (12.0 * h * h);
+    c.ko[d] = sigma / (64.0 * h);
+    c.ih[d] = 1.0 / h;
+  }
+  c.mix[0] = 1.0 / (144.0 * g->h[0] * g->h[1]);
+  c.mix[1] = 1.0 / (144.0 * g->h[0] * g->h[2]);
+  c.mix[2] = 1.0 / (144.0 * g->h[1] * g->h[2]);
+  return c;
+}
+
+DevGrid make_devgrid(const cosmos_grid* g) {
+  DevGrid d;
+  d.nx = g->nx;
+  d.ny = g->ny;
+  d.nz = g->nz;
+  d.pitch = g->pitch;
+  d.fstride = (long)g->pitch * g->ny * g->nz;
+  for (int k = 0; k < 3; ++k) d.h[k] = g->h[k];
+  return d;
+}
+
+static double K_ref(const cosmos_params* p, double t) {
+  if (p->H0 == 0.0) return 0.0;
+  return -3.0 * p->H0 / (1.0 + 1.5 * (1.0 + p->w) * p->H0 * (t - p->t0));
+}
+
+static AlgebraParams algebra_params(const cosmos_params* p, double t) {
+  AlgebraParams a;
+  a.eta = p->eta;
+  a.Kref = K_ref(p, t);
+  a.lapse_c1 = p->slicing == 0 ? 2.0 : 0.0;
+  a.lapse_c2 = p->slicing == 0 ? 0.0 : 1.0;
+  a.shift_on = p->shift ? 1.0 : 0.0;
+  a.w = p->w;
+  return a;
+}
+
+static long n_blocks(const DevGrid& g) {
+  const dim3 b = point_grid(g);
+  return (long)b.x * b.y * b.z;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int validate(const cosmos_grid* g, const cosmos_params* p) {
+  if (!g || !p) return COSMOS_EINVAL;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->pitch < g->nx) return COSMOS_EINVAL;
+  if (g->nz > 65535 || (g->ny + BY - 1) / BY > 65535) return COSMOS_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (!(g->h[d] > 0.0) || !isfinite(g->h[d])) return COSMOS_EINVAL;
+  if (p->slicing != 0 && p->slicing != 1) return COSMOS_EINVAL;
+  if (p->shift != 0 && p->shift != 1) return COSMOS_EINVAL;
+  if (p->fluid != 0 && p->fluid != 1) return COSMOS_EINVAL;
+  if (p->scalar != 0 && p->scalar != 1) return COSMOS_EINVAL;
+  if (!(p->ko_sigma >= 0.0) || !isfinite(p->eta)) return COSMOS_EINVAL;
+  if (p->fluid && !(p->w > 0.0 && p->w <= 1.0)) return COSMOS_EINVAL;
+  return COSMOS_OK;
+}
+
+// Workspace sub-buffers (each 256-byte aligned), in doubles from ws.
+struct WsLayout {
+  size_t prim, flux, stageA, stageB, acc, hm, partial, final_, total_bytes;
+};
+
+static WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
+  const DevGrid d = make_devgrid(g);
+  const size_t fs = (size_t)d.fstride;
+  const int nf = 24 + 4 * p->fluid + 2 * p->scalar;
+  WsLayout L;
+  memset(&L, 0, sizeof(L));
+  size_t off = 0;
+  auto take = [&](size_t doubles) {
+    size_t o = off;
+    off += align256(doubles * sizeof(double));
+    return o / sizeof(double);
+  };
+  const bool fluid = p->fluid != 0;
+  if (op == COSMOS_OP_RHS || op == COSMOS_OP_RK4) {
+    if (fluid) {
+      L.prim = take(4 * fs);
+      L.flux = take(12 * fs);
+    }
+    if (op == COSMOS_OP_RK4) {
+      L.stageA = take(nf * fs);
+      L.stageB = take(nf * fs);
+      L.acc = take(nf * fs);
+    }
+  } else if (op == COSMOS_OP_CONSTRAINTS || op == COSMOS_OP_INIT) {
+    if (fluid) L.prim = take(4 * fs);
+    if (op == COSMOS_OP_INIT) L.hm = take(4 * fs);
+    L.partial = take(8 * n_blocks(d));
+    L.final_ = take(8);
+  }
+  L.total_bytes = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+__global__ void reduce_partials(const double* __restrict__ part, long nb, double* __restrict__ out) {
+  // one block of 256 threads; fixed summation order
+  __shared__ double s[256][8];
+  double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      r[m] += part[b * 8 + m];
+      r[4 + m] = fmax(r[4 + m], part[b * 8 + 4 + m]);
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) s[threadIdx.x][m] = r[m];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        s[threadIdx.x][m] += s[threadIdx.x + w][m];
+        s[threadIdx.x][4 + m] = fmax(s[threadIdx.x][4 + m], s[threadIdx.x + w][4 + m]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int m = 0; m < 8; ++m) out[m] = s[0][m];
+}
+
+struct InitArgs {
+  DevGrid g;
+  double x0[3];
+  int nf;
+  cosmos_id id;
+  double H0;
+};
+
+__global__ void init_metric_kernel(const InitArgs a, double* __restrict__ U) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= a.g.nx || j >= a.g.ny) return;
+  const long c = ((long)k * a.g.ny + j) * a.g.pitch + i;
+  const long fs = a.g.fstride;
+  double v[30];
+  for (int f = 0; f < 30; ++f) v[f] = 0.0;
+  const double x[3] = {a.x0[0] + i * a.g.h[0], a.x0[1] + j * a.g.h[1], a.x0[2] + k * a.g.h[2]};
+  if (a.id.kind == 0) {
+    // gauge wave: gamma_xx = H, alpha = sqrt(H), K_xx = -d_t H / (2 sqrt(H))
+    const double Lx = a.g.nx * a.g.h[0];
+    const double ph = 2.0 * PI * (x[0] - a.id.t) / Lx;
+    const double H = 1.0 - a.id.A * sin(ph);
+    const double dtH = a.id.A * (2.0 * PI / Lx) * cos(ph);
+    const double sH = sqrt(H);
+    const double Kxx = -dtH / (2.0 * sH);
+    const double trK = Kxx / H;
+    const double chi = pow(H, -1.0 / 3.0);
+    v[0] = chi;
+    v[1] = pow(H, 2.0 / 3.0);
+    v[4] = chi;
+    v[6] = chi;
+    v[7] = trK;
+    v[8] = chi * (Kxx - H * trK / 3.0);
+    v[11] = -chi * trK / 3.0;
+    v[13] = -chi * trK / 3.0;
+    v[14] = 2.0 / 3.0 * pow(H, -5.0 / 3.0) * (-dtH);  // -d_x gt^xx, d_x H = -d_t H
+    v[17] = sH;
+  } else {
+    // FLRW + zeta, leading gradient order: gamma_ij = a0^2 exp(2 zeta) delta_ij
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double u = (x[d] - a.id.center[d]) / a.id.q[d];
+      r2 += u * u;
+    }
+    const double zeta = a.id.mu * exp(-r2 / (2.0 * a.id.sigma * a.id.sigma));
+    v[0] = exp(-2.0 * zeta) / (a.id.a0 * a.id.a0);
+    v[1] = v[4] = v[6] = 1.0;
+    v[7] = -3.0 * a.H0;
+    v[17] = 1.0;
+  }
+  for (int f = 0; f < a.nf; ++f) U[f * fs + c] = v[f];
+}
+
+// tau~ = sqrt(gamma) E with E = (R + 2/3 K^2 - At.At)/(16 pi) = H_vacuum/(16 pi)
+__global__ void init_tau_kernel(const DevGrid g, const double* __restrict__ hm, double* __restrict__ U) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long c = ((long)k * g.ny + j) * g.pitch + i;
+  const double chi = U[c];
+  const double E = hm[c] / (16.0 * PI);
+  U[24 * g.fstride + c] = E / (chi * sqrt(chi));
+}
+
+__global__ void fp64_fma_chains(double* __restrict__ out, int iters, double a, double b) {
+  double acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = (threadIdx.x + c) * 1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = fma(acc[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += acc[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+typedef cudaError_t (*StageLauncher)(const StageArgs&, int, cudaStream_t);
+typedef cudaError_t (*ConstraintLauncher)(const ConstraintArgs&, cudaStream_t);
+
+static StageLauncher stage_launcher(const cosmos_params* p) {
+  if (p->fluid && p->scalar) return launch_stage_fluid_scalar;
+  if (p->fluid) return launch_stage_fluid;
+  if (p->scalar) return launch_stage_scalar;
+  return launch_stage_vac;
+}
+
+static ConstraintLauncher constraint_launcher(const cosmos_params* p) {
+  if (p->fluid && p->scalar) return launch_constraints_fluid_scalar;
+  if (p->fluid) return launch_constraints_fluid;
+  if (p->scalar) return launch_constraints_scalar;
+  return launch_constraints_vac;
+}
+
+// Shared body of cosmos_rhs / cosmos_rk4_stage.
+static int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n,
+                     double* out, double* acc, double t_stage, double cdt, double bk, double* ws,
+                     const WsLayout& L, cudaStream_t s) {
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = make_devgrid(g);
+  a.c = make_coef(g, p->ko_sigma);
+  a.ap = algebra_params(p, t_stage);
+  a.U = U_s;
+  a.U0 = U_n;
+  a.U0w = U_n;
+  a.out = out;
+  a.acc = acc;
+  a.cdt = cdt;
+  a.bk = bk;
+  if (p->fluid) {
+    double* prim = ws + L.prim;
+    double* flux = ws + L.flux;
+    CK(launch_fluid_prim(a.g, U_s, prim, p->w, s));
+    CK(launch_fluid_flux(a.g, U_s, prim, flux, p->w, 24, s));
+    a.prim = prim;
+    a.flux = flux;
+  }
+  CK(stage_launcher(p)(a, mode, s));
+  return COSMOS_OK;
+}
+
+static int check_ws(const WsLayout& L, void* ws, size_t ws_bytes) {
+  if (L.total_bytes == 0) return COSMOS_OK;
+  if (!ws) return COSMOS_EINVAL;
+  if (ws_bytes < L.total_bytes) return COSMOS_EWORKSPACE;
+  if (((uintptr_t)ws & 255u) != 0) return COSMOS_EALIGN;
+  return COSMOS_OK;
+}
+
+}  // namespace cosmos
+
+using namespace cosmos;
+
+extern "C" {
+
+int cosmos_nfields(const cosmos_params* p) {
+  if (!p) return COSMOS_EINVAL;
+  return 24 + 4 * (p->fluid != 0) + 2 * (p->scalar != 0);
+}
+
+size_t cosmos_field_stride(const cosmos_grid* g) {
+  if (!g) return 0;
+  return (size_t)g->pitch * g->ny * g->nz;
+}
+
+size_t cosmos_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int op) {
+  if (validate(g, p) != COSMOS_OK) return 0;
+  return ws_layout(g, p, op).total_bytes;
+}
+
+int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
+                     size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!id || !state) return COSMOS_EINVAL;
+  if (!aligned16(state)) return COSMOS_EALIGN;
+  if (id->kind != 0 && id->kind != 1) return COSMOS_EINVAL;
+  if (id->kind == 0 && p->fluid) return COSMOS_EINVAL;  // the gauge wave is vacuum
+  if (id->kind == 1 && (!(id->sigma > 0.0) || !(id->a0 > 0.0) || !(id->q[0] > 0.0) || !(id->q[1] > 0.0) ||
+                        !(id->q[2] > 0.0)))
+    return COSMOS_EINVAL;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_INIT);
+  const bool need_ws = (id->kind == 1 && p->fluid);
+  if (need_ws && (e = check_ws(L, ws, ws_bytes))) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  InitArgs a;
+  a.g = make_devgrid(g);
+  for (int d = 0; d < 3; ++d) a.x0[d] = g->x0[d];
+  a.nf = cosmos_nfields(p);
+  a.id = *id;
+  a.H0 = p->H0;
+  init_metric_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a, state);
+  CK(cudaGetLastError());
+  if (need_ws) {
+    double* w = (double*)ws;
+    ConstraintArgs c;
+    memset(&c, 0, sizeof(c));
+    c.g = a.g;
+    c.c = make_coef(g, 0.0);
+    cosmos_params pv = *p;
+    pv.fluid = 0;
+    pv.scalar = 0;
+    c.ap = algebra_params(&pv, 0.0);
+    c.U = state;
+    c.hm = w + L.hm;
+    c.partial = w + L.partial;
+    CK(launch_constraints_vac(c, s));
+    init_tau_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a.g, w + L.hm, state);
+    CK(cudaGetLastError());
+  }
+  return COSMOS_OK;
+}
+
+int cosmos_rhs(const cosmos_grid* g, const cosmos_params* p, const double* state, double* rhs, double t, void* ws,
+               size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state || !rhs || state == rhs) return COSMOS_EINVAL;
+  if (!aligned16(state) || !aligned16(rhs)) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RHS);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  return run_stage(g, p, MODE_RHS, state, nullptr, rhs, nullptr, t, 0.0, 0.0, (double*)ws, L,
+                   (cudaStream_t)stream);
+}
+
+int cosmos_rk4_stage(const cosmos_grid* g, const cosmos_params* p, int stage, const double* U_s, double* U_n,
+                     double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (stage < 1 || stage > 4 || !U_s || !U_n || !acc) return COSMOS_EINVAL;
+  if (stage < 4 && !U_next) return COSMOS_EINVAL;
+  if (U_s == acc || (stage < 4 && (U_s == U_next || U_next == acc || U_next == U_n))) return COSMOS_EINVAL;
+  if (stage == 4 && U_s == U_n) return COSMOS_EINVAL;
+  if (!aligned16(U_s) || !aligned16(U_n) || !aligned16(acc) || (U_next && !aligned16(U_next))) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RHS);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
+  static const int modes[4] = {MODE_S1, MODE_S23, MODE_S23, MODE_S4};
+  const double cdt = stage == 1 || stage == 2 ? 0.5 * dt : (stage == 3 ? dt : dt / 6.0);
+  return run_stage(g, p, modes[stage - 1], U_s, U_n, U_next, acc, t + c_stage[stage - 1] * dt, cdt, 2.0,
+                   (double*)ws, L, (cudaStream_t)stream);
+}
+
+int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
+                    size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state) return COSMOS_EINVAL;
+  if (!aligned16(state)) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RK4);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  double* w = (double*)ws;
+  double* A = w + L.stageA;
+  double* B = w + L.stageB;
+  double* acc = w + L.acc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double dt2 = 0.5 * dt;
+  if ((e = run_stage(g, p, MODE_S1, state, state, A, acc, t, dt2, 2.0, w, L, s))) return e;
+  if ((e = run_stage(g, p, MODE_S23, A, state, B, acc, t + dt2, dt2, 2.0, w, L, s))) return e;
+  if ((e = run_stage(g, p, MODE_S23, B, state, A, acc, t + dt2, dt, 2.0, w, L, s))) return e;
+  return run_stage(g, p, MODE_S4, A, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s);
+}
+
+int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
+                       double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!host_in || !host_out || !dev_state || steps < 0) return COSMOS_EINVAL;
+  const size_t bytes = cosmos_field_stride(g) * (size_t)cosmos_nfields(p) * sizeof(double);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(dev_state, host_in, bytes, cudaMemcpyHostToDevice, s));
+  for (int n = 0; n < steps; ++n)
+    if ((e = cosmos_rk4_step(g, p, dev_state, t + n * dt, dt, ws, ws_bytes, stream))) return e;
+  CK(cudaMemcpyAsync(host_out, dev_state, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return COSMOS_OK;
+}
+
+int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
+                       double norms_host[8], void* ws, size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state || !norms_host) return COSMOS_EINVAL;
+  if (!aligned16(state) || (ham_mom && !aligned16(ham_mom))) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_CONSTRAINTS);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* w = (double*)ws;
+  ConstraintArgs c;
+  memset(&c, 0, sizeof(c));
+  c.g = make_devgrid(g);
+  c.c = make_coef(g, 0.0);
+  c.ap = algebra_params(p, 0.0);
+  c.U = state;
+  c.hm = ham_mom;
+  c.partial = w + L.partial;
+  if (p->fluid) {
+    CK(launch_fluid_prim(c.g, state, w + L.prim, p->w, s));
+    c.prim = w + L.prim;
+  }
+  CK(constraint_launcher(p)(c, s));
+  reduce_partials<<<1, 256, 0, s>>>(w + L.partial, n_blocks(c.g), w + L.final_);
+  CK(cudaGetLastError());
+  double r[8];
+  CK(cudaMemcpyAsync(r, w + L.final_, sizeof(r), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double npts = (double)g->nx * g->ny * g->nz;
+  for (int m = 0; m < 4; ++m) {
+    norms_host[m] = sqrt(r[m] / npts);
+    norms_host[4 + m] = r[4 + m];
+  }
+  return COSMOS_OK;
+}
+
+int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream) {
+  if (!scratch || !flops_out) return COSMOS_EINVAL;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (sms > 152) sms = 152;  // scratch holds 152 * 8 * 256 doubles
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  fp64_fma_chains<<<blocks, threads, 0, s>>>(scratch, iters, 0.999999, 1e-7);  // warm-up
+  CK(cudaEventRecord(e0, s));
+  fp64_fma_chains<<<blocks, threads, 0, s>>>(scratch, iters, 0.999999, 1e-7);
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *flops_out = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
+  return COSMOS_OK;
+}
+
+int cosmos_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* cosmos_strerror(int code) {
+  switch (code) {
+    case COSMOS_OK: return "ok";
+    case COSMOS_EINVAL: return "invalid argument";
+    case COSMOS_ECUDA: return "CUDA runtime error (see cosmos_last_cuda_error)";
+    case COSMOS_EWORKSPACE: return "workspace too small";
+    case COSMOS_EALIGN: return "pointer not aligned (16 bytes; workspace 256 bytes)";
+    case COSMOS_ENONFINITE: return "non-finite or unphysical state";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

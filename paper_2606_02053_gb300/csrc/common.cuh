@@ -1,0 +1,113 @@
+// Internal definitions shared by the CUDA translation units of libcosmos_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cosmos.h"
+#include "generated/bssn_algebra.cuh"
+#include "generated/fluid_algebra.cuh"
+
+namespace cosmos {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr int BX = 32;  // threads per block along x (one warp = one row)
+constexpr int BY = 4;   // rows per block
+
+// Grid description as the kernels see it.
+struct DevGrid {
+  int nx, ny, nz, pitch;
+  long fstride;  // doubles between fields
+  double h[3];
+};
+
+// Periodic neighbour offsets of one point for offsets -3..3 per direction,
+// already multiplied by the memory stride of that direction.
+struct Nbr {
+  long x[7], y[7], z[7];
+  long c;  // offset of the point itself
+};
+
+__device__ __forceinline__ int wrap_index(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ Nbr make_nbr(const DevGrid& g, int i, int j, int k) {
+  Nbr n;
+  const long row = g.pitch, plane = (long)g.pitch * g.ny;
+#pragma unroll
+  for (int o = -3; o <= 3; ++o) {
+    n.x[o + 3] = wrap_index(i + o, g.nx);
+    n.y[o + 3] = wrap_index(j + o, g.ny) * row;
+    n.z[o + 3] = wrap_index(k + o, g.nz) * plane;
+  }
+  n.c = n.z[3] + n.y[3] + n.x[3];
+  return n;
+}
+
+// Offset of the point displaced by (dx, dy, dz), |d| <= 3.
+__device__ __forceinline__ long at(const Nbr& n, int dx, int dy, int dz) {
+  return n.z[dz + 3] + n.y[dy + 3] + n.x[dx + 3];
+}
+
+__device__ __forceinline__ double ldg(const double* __restrict__ p, long o) { return __ldg(p + o); }
+
+// Stencil coefficients derived on the host from the grid spacing.
+struct Coef {
+  double d1a[3], d1b[3];  // D1 = a (f+1 - f-1) - b (f+2 - f-2):   a = 8/(12h), b = 1/(12h)
+  double d2a[3], d2b[3];  // D2 = a s1 - b s2:                         a = 16/(12h^2), b = 1/(12h^2)
+  double mix[3];          // mixed xy, xz, yz:  1/(144 h_a h_b)
+  double ko[3];           // sigma/(64 h_d)
+  double ih[3];           // 1/h_d (flux divergence)
+};
+
+Coef make_coef(const cosmos_grid* g, double sigma);
+DevGrid make_devgrid(const cosmos_grid* g);
+
+// RK4 stage modes of the fused kernel
+enum StageMode { MODE_RHS = 0, MODE_S1 = 1, MODE_S23 = 2, MODE_S4 = 3 };
+
+struct StageArgs {
+  DevGrid g;
+  Coef c;
+  AlgebraParams ap;
+  const double* __restrict__ U;    // stencil input (stage state)
+  const double* __restrict__ U0;   // U_n (pointwise) -- MODE_S1/S23/S4
+  double* U0w;                     // U_n written in MODE_S4
+  double* out;                     // MODE_RHS: rhs;  MODE_S1/S23: U_next
+  double* acc;                     // accumulator
+  const double* __restrict__ prim; // fluid primitives [4][pts] (fluid only)
+  const double* __restrict__ flux; // fluid face fluxes [3][4][pts] (fluid only)
+  double cdt;                      // dt * c_{s+1}, or dt/6 in MODE_S4
+  double bk;                       // accumulator weight (2 for stages 2, 3)
+};
+
+struct ConstraintArgs {
+  DevGrid g;
+  Coef c;
+  AlgebraParams ap;
+  const double* __restrict__ U;
+  const double* __restrict__ prim;
+  double* hm;        // [4][pts] or null
+  double* partial;   // [nblocks][8]: sum of squares (4) and max abs (4)
+};
+
+// Launchers implemented per matter variant (stage_<variant>.cu).
+cudaError_t launch_stage_vac(const StageArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_stage_fluid(const StageArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_stage_scalar(const StageArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_stage_fluid_scalar(const StageArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_constraints_vac(const ConstraintArgs& a, cudaStream_t s);
+cudaError_t launch_constraints_fluid(const ConstraintArgs& a, cudaStream_t s);
+cudaError_t launch_constraints_scalar(const ConstraintArgs& a, cudaStream_t s);
+cudaError_t launch_constraints_fluid_scalar(const ConstraintArgs& a, cudaStream_t s);
+
+// fluid.cu
+cudaError_t launch_fluid_prim(const DevGrid& g, const double* U, double* prim, double w, cudaStream_t s);
+cudaError_t launch_fluid_flux(const DevGrid& g, const double* U, const double* prim, double* flux, double w,
+                              int nf_offset_fluid, cudaStream_t s);
+
+inline dim3 point_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
+
+}  // namespace cosmos

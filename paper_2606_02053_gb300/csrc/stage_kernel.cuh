@@ -1,0 +1,233 @@
+// Fused BSSN right-hand side + RK4 stage kernel (one grid point per thread).
+//
+// Per point: 4th-order centred first and second derivatives of every field
+// the algebra needs (loaded straight from global memory through the
+// read-only cache -- the sweep is bound by the FP64 pipe, not by memory),
+// the generated pointwise algebra, 6th-derivative Kreiss-Oliger dissipation
+// on the non-fluid fields, the Kurganov-Tadmor flux divergence on the fluid
+// fields, and the RK4 stage combine.  Every stencil is written so that its
+// large cancellations happen in exact neighbour differences.
+#pragma once
+
+#include "common.cuh"
+
+namespace cosmos {
+
+template <int D>
+__device__ __forceinline__ long disp(const Nbr& n, int o) {
+  if (D == 0) return n.z[3] + n.y[3] + n.x[o + 3];
+  if (D == 1) return n.z[3] + n.y[o + 3] + n.x[3];
+  return n.z[o + 3] + n.y[3] + n.x[3];
+}
+
+template <int A, int B>
+__device__ __forceinline__ long disp2(const Nbr& n, int oa, int ob) {
+  int o[3] = {0, 0, 0};
+  o[A] = oa;
+  o[B] = ob;
+  return n.z[o[2] + 3] + n.y[o[1] + 3] + n.x[o[0] + 3];
+}
+
+// D_d f = a (f+1 - f-1) - b (f+2 - f-2)
+template <int D>
+__device__ __forceinline__ double fd1(const double* __restrict__ F, const Nbr& n, const Coef& c) {
+  const double a = ldg(F, disp<D>(n, 1)) - ldg(F, disp<D>(n, -1));
+  const double b = ldg(F, disp<D>(n, 2)) - ldg(F, disp<D>(n, -2));
+  return a * c.d1a[D] - b * c.d1b[D];
+}
+
+// D_dd f = a ((f+1 - f0) + (f-1 - f0)) - b ((f+2 - f0) + (f-2 - f0))
+template <int D>
+__device__ __forceinline__ double fd2(const double* __restrict__ F, const Nbr& n, const Coef& c, double f0) {
+  const double s1 = (ldg(F, disp<D>(n, 1)) - f0) + (ldg(F, disp<D>(n, -1)) - f0);
+  const double s2 = (ldg(F, disp<D>(n, 2)) - f0) + (ldg(F, disp<D>(n, -2)) - f0);
+  return s1 * c.d2a[D] - s2 * c.d2b[D];
+}
+
+// D_A D_B f = [64 Q11 - 8 (Q12 + Q21) + Q22] / (144 h_A h_B),
+// Q_pq = (f(p, q) - f(-p, q)) - (f(p, -q) - f(-p, -q))  (the 16-point product stencil)
+template <int A, int B>
+__device__ __forceinline__ double fdmix(const double* __restrict__ F, const Nbr& n, double cm) {
+  double q[2][2];
+#pragma unroll
+  for (int p = 1; p <= 2; ++p)
+#pragma unroll
+    for (int r = 1; r <= 2; ++r) {
+      const double u = ldg(F, disp2<A, B>(n, p, r)) - ldg(F, disp2<A, B>(n, -p, r));
+      const double v = ldg(F, disp2<A, B>(n, p, -r)) - ldg(F, disp2<A, B>(n, -p, -r));
+      q[p - 1][r - 1] = u - v;
+    }
+  const double cross = q[0][1] + q[1][0];
+  return q[0][0] * (64.0 * cm) + (q[1][1] * cm - cross * (8.0 * cm));
+}
+
+// rhs + sigma/64 sum_d (1/h_d) [ (f+3 + f-3) - 6 (f+2 + f-2) + 15 (f+1 + f-1) - 20 f0 ]
+template <int D>
+__device__ __forceinline__ double ko_dir(const double* __restrict__ F, const Nbr& n, double f0) {
+  const double s1 = ldg(F, disp<D>(n, 1)) + ldg(F, disp<D>(n, -1));
+  const double s2 = ldg(F, disp<D>(n, 2)) + ldg(F, disp<D>(n, -2));
+  const double s3 = ldg(F, disp<D>(n, 3)) + ldg(F, disp<D>(n, -3));
+  return (s3 - 6.0 * s2) + (15.0 * s1 - 20.0 * f0);
+}
+
+__device__ __forceinline__ double ko_add(const double* __restrict__ F, const Nbr& n, const Coef& c, double f0,
+                                         double r) {
+  r = fma(c.ko[0], ko_dir<0>(F, n, f0), r);
+  r = fma(c.ko[1], ko_dir<1>(F, n, f0), r);
+  r = fma(c.ko[2], ko_dir<2>(F, n, f0), r);
+  return r;
+}
+
+// Inputs of the generated algebra at one point (layout documented in codegen/bssn.py).
+template <class T>
+__device__ __forceinline__ void gather(const double* __restrict__ U, const double* __restrict__ prim, const Nbr& n,
+                                       const Coef& c, long fs, double* in) {
+#pragma unroll
+  for (int f = 0; f < T::NF; ++f) in[f] = ldg(U + (long)f * fs, n.c);
+#pragma unroll
+  for (int m = 0; m < T::ND1; ++m) {
+    const double* F = U + (long)T::d1_field(m) * fs;
+    in[T::NF + 3 * m + 0] = fd1<0>(F, n, c);
+    in[T::NF + 3 * m + 1] = fd1<1>(F, n, c);
+    in[T::NF + 3 * m + 2] = fd1<2>(F, n, c);
+  }
+#pragma unroll
+  for (int m = 0; m < T::ND2; ++m) {
+    const int f = T::d2_field(m);
+    const double* F = U + (long)f * fs;
+    const double f0 = in[f];
+    const int b = T::NF + 3 * T::ND1 + 6 * m;
+    in[b + 0] = fd2<0>(F, n, c, f0);
+    in[b + 1] = fdmix<0, 1>(F, n, c.mix[0]);
+    in[b + 2] = fdmix<0, 2>(F, n, c.mix[1]);
+    in[b + 3] = fd2<1>(F, n, c, f0);
+    in[b + 4] = fdmix<1, 2>(F, n, c.mix[2]);
+    in[b + 5] = fd2<2>(F, n, c, f0);
+  }
+  if constexpr (T::FLUID) in[T::NIN - 1] = ldg(prim, n.c);
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(BX* BY, 2) stage_kernel(const StageArgs a) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= a.g.nx || j >= a.g.ny) return;
+  const Nbr n = make_nbr(a.g, i, j, k);
+  const long fs = a.g.fstride;
+  double in[T::NIN];
+  gather<T>(a.U, a.prim, n, a.c, fs, in);
+  double out[T::NF];
+  T::rhs(in, out, a.ap);
+#pragma unroll
+  for (int f = 0; f < T::NF; ++f) {
+    double r = out[f];
+    if (T::FLUID && f >= 24 && f < 28) {
+      const double* H = a.flux + (long)(f - 24) * fs;  // direction d at H + 4 d fs
+      r -= (ldg(H, n.c) - ldg(H, disp<0>(n, -1))) * a.c.ih[0];
+      r -= (ldg(H + 4 * fs, n.c) - ldg(H + 4 * fs, disp<1>(n, -1))) * a.c.ih[1];
+      r -= (ldg(H + 8 * fs, n.c) - ldg(H + 8 * fs, disp<2>(n, -1))) * a.c.ih[2];
+    } else {
+      r = ko_add(a.U + (long)f * fs, n, a.c, in[f], r);
+    }
+    const long o = (long)f * fs + n.c;
+    if constexpr (MODE == MODE_RHS) {
+      a.out[o] = r;
+    } else if constexpr (MODE == MODE_S1) {
+      a.out[o] = fma(a.cdt, r, ldg(a.U0, o));
+      a.acc[o] = r;
+    } else if constexpr (MODE == MODE_S23) {
+      a.out[o] = fma(a.cdt, r, ldg(a.U0, o));
+      a.acc[o] = fma(a.bk, r, a.acc[o]);
+    } else {
+      a.U0w[o] = fma(a.cdt, a.acc[o] + r, a.U0w[o]);
+    }
+  }
+}
+
+// Constraints H, M^i per point plus per-block partial norms.
+template <class T>
+__global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintArgs a) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  const bool valid = (i < a.g.nx) && (j < a.g.ny);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (valid) {
+    const Nbr n = make_nbr(a.g, i, j, k);
+    const long fs = a.g.fstride;
+    double in[T::NIN];
+    gather<T>(a.U, a.prim, n, a.c, fs, in);
+    T::constraints(in, v, a.ap);
+    if (a.hm) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) a.hm[(long)m * fs + n.c] = v[m];
+    }
+  }
+  double r[8];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    r[m] = v[m] * v[m];
+    r[4 + m] = fabs(v[m]);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      r[m] += __shfl_down_sync(0xffffffffu, r[m], off);
+      r[4 + m] = fmax(r[4 + m], __shfl_down_sync(0xffffffffu, r[4 + m], off));
+    }
+  }
+  __shared__ double red[BY][8];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) red[threadIdx.y][m] = r[m];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double s[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) s[m] = red[0][m];
+    for (int w = 1; w < BY; ++w) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        s[m] += red[w][m];
+        s[4 + m] = fmax(s[4 + m], red[w][4 + m]);
+      }
+    }
+    const long b = ((long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) a.partial[b * 8 + m] = s[m];
+  }
+}
+
+#define COSMOS_DEFINE_VARIANT(NAME, IS_FLUID, IS_SCALAR)                                                          \
+  struct T_##NAME {                                                                                             \
+    static constexpr int NF = alg_##NAME::NF, ND1 = alg_##NAME::ND1, ND2 = alg_##NAME::ND2,                     \
+                         NIN = alg_##NAME::NIN;                                                                 \
+    static constexpr bool FLUID = IS_FLUID, SCALAR = IS_SCALAR;                                                 \
+    __device__ static constexpr int d1_field(int m) { return alg_##NAME::d1_field(m); }                        \
+    __device__ static constexpr int d2_field(int m) { return alg_##NAME::d2_field(m); }                        \
+    __device__ static __forceinline__ void rhs(const double* in, double* out, const AlgebraParams& p) {          \
+      alg_##NAME::rhs(in, out, p);                                                                              \
+    }                                                                                                           \
+    __device__ static __forceinline__ void constraints(const double* in, double* out, const AlgebraParams& p) {  \
+      alg_##NAME::constraints(in, out, p);                                                                      \
+    }                                                                                                           \
+  };                                                                                                            \
+  cudaError_t launch_stage_##NAME(const StageArgs& a, int mode, cudaStream_t s) {                               \
+    const dim3 grid = point_grid(a.g), block(BX, BY);                                                          \
+    switch (mode) {                                                                                             \
+      case MODE_RHS: stage_kernel<T_##NAME, MODE_RHS><<<grid, block, 0, s>>>(a); break;                        \
+      case MODE_S1: stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(a); break;                          \
+      case MODE_S23: stage_kernel<T_##NAME, MODE_S23><<<grid, block, 0, s>>>(a); break;                        \
+      default: stage_kernel<T_##NAME, MODE_S4><<<grid, block, 0, s>>>(a); break;                               \
+    }                                                                                                           \
+    return cudaGetLastError();                                                                                  \
+  }                                                                                                             \
+  cudaError_t launch_constraints_##NAME(const ConstraintArgs& a, cudaStream_t s) {                              \
+    constraint_kernel<T_##NAME><<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a);                                    \
+    return cudaGetLastError();                                                                                  \
+  }
+
+}  // namespace cosmos

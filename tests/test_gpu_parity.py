@@ -1,0 +1,246 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (per field f, oracle o, GPU g):
+    err_f = max|g - o| / max(max|o_f|, 1e-12 * max_all|o|)
+    right-hand side:  err_f <= 1e-12;   after the stated step counts: <= 1e-10.
+The GPU contracts multiply-adds into FMA and orders sums differently; all
+stencils difference neighbouring values first on both sides, so the
+remaining rounding differences are a few ulps of each term.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-12
+STEP_TOL = 1e-10
+
+
+def field_errors(gpu, ref):
+    gpu = gpu.reshape(gpu.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    floor = 1e-12 * np.abs(ref).max()
+    den = np.maximum(np.abs(ref).max(axis=1), floor)
+    return np.abs(gpu - ref).max(axis=1) / den
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2606_02053_gb300 import build, cosmos
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    cosmos.lib()
+    return cosmos
+
+
+def oracle_params(O, Cp):
+    return O.params_array(slicing=Cp.slicing, shift=Cp.shift, eta=Cp.eta, ko_sigma=Cp.ko_sigma, w=Cp.w,
+                          fluid=Cp.fluid, scalar=Cp.scalar, H0=Cp.H0, t0=Cp.t0)
+
+
+def run_rhs(C, O, n, h, params, state, t=0.0, pitch=None):
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    g = C.make_grid(n, h, pitch=pitch)
+    ev = Evolution(g, params)
+    ev.set_state(state)
+    r = ev.get(ev.rhs(t))
+    og = O.OGrid(n, h)
+    ref = O.rhs(og, oracle_params(O, params), state, t)
+    return r, ref
+
+
+@pytest.mark.parametrize("fluid,scalar", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("n,pitch", [((20, 12, 9), None), ((37, 13, 11), 40), ((33, 8, 16), None)])
+def test_rhs_parity_smooth_random_state(C, O, fluid, scalar, n, pitch):
+    from paper_2606_02053_gb300 import inputs
+
+    p = C.make_params(slicing=0, shift=1, fluid=fluid, scalar=scalar, eta=1.7, ko_sigma=0.1, H0=2.0 * fluid)
+    s = inputs.smooth_state(n, seed=100 + 7 * fluid + scalar, fluid=fluid, scalar=scalar)
+    r, ref = run_rhs(C, O, n, 1.0 / n[0], p, s, t=0.013, pitch=pitch)
+    err = field_errors(r, ref)
+    assert err.max() <= RHS_TOL, (err.argmax(), err.max(), err)
+
+
+@pytest.mark.parametrize("slicing,shift", [(1, 0), (0, 0), (1, 1)])
+def test_rhs_parity_gauge_options(C, O, slicing, shift):
+    from paper_2606_02053_gb300 import inputs
+
+    n = (16, 16, 16)
+    p = C.make_params(slicing=slicing, shift=shift, eta=0.5, ko_sigma=0.3)
+    s = inputs.smooth_state(n, seed=5)
+    r, ref = run_rhs(C, O, n, 0.0625, p, s)
+    assert field_errors(r, ref).max() <= RHS_TOL
+
+
+def test_rhs_parity_thin_and_tiny_grids(C, O):
+    from paper_2606_02053_gb300 import inputs
+
+    p = C.make_params()
+    for n in [(16, 1, 1), (8, 3, 2), (1, 1, 1), (5, 7, 1)]:
+        s = inputs.smooth_state(n, seed=9)
+        r, ref = run_rhs(C, O, n, 0.1, p, s)
+        assert field_errors(r, ref).max() <= RHS_TOL, n
+
+
+def test_flat_space_rhs_is_exactly_zero(C, O):
+    n = (12, 9, 7)
+    p = C.make_params()
+    s = np.zeros((24, n[2], n[1], n[0]))
+    s[0] = 0.7
+    s[1] = s[4] = s[6] = 1.0
+    s[17] = 1.3
+    s[18] = 0.2
+    r, _ = run_rhs(C, O, n, 0.1, p, s)
+    assert np.all(r == 0.0)
+
+
+@pytest.mark.parametrize("fluid", [0, 1])
+def test_rk4_step_parity(C, O, fluid):
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = (24, 20, 18)
+    h = 1.0 / 24
+    p = C.make_params(fluid=fluid, H0=3.0 * fluid)
+    s = inputs.smooth_state(n, seed=33 + fluid, fluid=fluid)
+    ev = Evolution(C.make_grid(n, h), p)
+    ev.set_state(s)
+    ev.step(0.1, 0.25 * h, steps=2)
+    ref = s.copy()
+    O.evolve(O.OGrid(n, h), oracle_params(O, p), ref, 0.1, 0.25 * h, 2)
+    assert field_errors(ev.get(), ref).max() <= STEP_TOL
+
+
+def test_rk4_stage_entry_point_composes_to_step(C):
+    """Four cosmos_rk4_stage calls equal one cosmos_rk4_step, bitwise."""
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = (16, 16, 16)
+    h = 1.0 / 16
+    p = C.make_params()
+    s = inputs.smooth_state(n, seed=4)
+    a = Evolution(C.make_grid(n, h), p)
+    a.set_state(s)
+    a.step(0.0, 0.01)
+    b = Evolution(C.make_grid(n, h), p)
+    b.set_state(s)
+    U1, U2, acc = (torch.empty_like(b.state) for _ in range(3))
+    ws = b.ws_rhs
+    for st, (src, dst) in enumerate([(b.state, U1), (U1, U2), (U2, U1), (U1, None)], start=1):
+        C.check(C.cosmos_rk4_stage(b.g, b.p, st, src, b.state, dst, acc, 0.0, 0.01, ws))
+    assert torch.equal(a.state, b.state)
+
+
+def test_gauge_wave_32_cube_20_steps(C, O):
+    """32^3 gauge wave, 1+log + Gamma-driver, dt = h/4, 20 steps."""
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n, h = 32, 1.0 / 32
+    p = C.make_params(slicing=0, shift=1, eta=2.0, ko_sigma=0.1)
+    ev = Evolution(C.make_grid(n, h), p)
+    ev.init(C.make_id(0, A=0.01))
+    op = oracle_params(O, p)
+    og = O.OGrid((n, n, n), h)
+    s0 = O.init(og, op, O.id_array(0, A=0.01))
+    assert field_errors(ev.get(), s0).max() <= 1e-13
+    ev.step(0.0, 0.25 * h, steps=20)
+    # the data is independent of y and z, so the oracle runs on an n x 1 x 1 grid (bitwise the same)
+    ot = O.OGrid((n, 1, 1), h)
+    ref = O.init(ot, op, O.id_array(0, A=0.01))
+    O.evolve(ot, op, ref, 0.0, 0.25 * h, 20)
+    g = ev.get()
+    assert field_errors(g[:, 7:8, 3:4, :], ref).max() <= STEP_TOL
+    assert np.abs(g - g[:, :1, :1, :]).max() <= 1e-13  # y, z invariance kept
+
+
+def test_gauge_wave_harmonic_closed_form_on_gpu(C):
+    """Harmonic slicing, frozen shift: the gauge wave is exact; 4th order."""
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    errs = []
+    for n in (16, 32):
+        h = 1.0 / n
+        p = C.make_params(slicing=1, shift=0)
+        ev = Evolution(C.make_grid((n, 4, 4), h), p)
+        ev.init(C.make_id(0, A=0.01))
+        steps = n
+        ev.step(0.0, 0.25 * h, steps=steps)
+        ex = Evolution(C.make_grid((n, 4, 4), h), p)
+        ex.init(C.make_id(0, A=0.01, t=steps * 0.25 * h))
+        errs.append(np.abs(ev.get() - ex.get()).max())
+    assert 12 < errs[0] / errs[1] < 20, errs
+
+
+def test_constraints_parity(C, O):
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    for fluid, scalar in [(0, 0), (1, 1)]:
+        n = (18, 14, 10)
+        h = 1.0 / 18
+        p = C.make_params(fluid=fluid, scalar=scalar)
+        s = inputs.smooth_state(n, seed=51, fluid=fluid, scalar=scalar)
+        ev = Evolution(C.make_grid(n, h), p)
+        ev.set_state(s)
+        hm, norms = ev.constraints(want_fields=True)
+        ref_hm, ref_norms = O.constraints(O.OGrid(n, h), oracle_params(O, p), s)
+        assert field_errors(hm, ref_hm).max() <= RHS_TOL
+        np.testing.assert_allclose(norms, ref_norms, rtol=1e-12)
+
+
+def test_flrw_zeta_init_parity_and_constraints(C, O):
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = 24
+    h = 1.0 / n
+    x0 = (-(n // 2) * h,) * 3
+    p = C.make_params(fluid=1, w=1.0 / 3.0, H0=40.0)
+    ev = Evolution(C.make_grid(n, h, x0=x0), p)
+    ev.init(C.make_id(1, mu=0.5, sigma=0.125, q=(1.0, 0.9, 1.1)))
+    og = O.OGrid((n, n, n), h, x0=x0)
+    ref = O.init(og, oracle_params(O, p), O.id_array(1, mu=0.5, sigma=0.125, q=(1.0, 0.9, 1.1)))
+    assert field_errors(ev.get(), ref).max() <= 1e-12
+    hm, norms = ev.constraints(want_fields=True)
+    assert np.abs(hm[0]).max() <= 1e-12 * 6.0 * 40.0 ** 2
+    assert np.abs(hm[1:]).max() == 0.0
+
+
+def test_flrw_zeta_evolution_parity_32(C, O):
+    """Radiation FLRW + Gaussian zeta (mu = 0.5, sigma = L/8, H0 L = 40) at 32^3, 40 steps."""
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = 32
+    h = 1.0 / n
+    x0 = (-(n // 2) * h,) * 3
+    p = C.make_params(fluid=1, w=1.0 / 3.0, H0=40.0)
+    ev = Evolution(C.make_grid(n, h, x0=x0), p)
+    ev.init(C.make_id(1, mu=0.5, sigma=0.125))
+    og = O.OGrid((n, n, n), h, x0=x0)
+    op = oracle_params(O, p)
+    ref = O.init(og, op, O.id_array(1, mu=0.5, sigma=0.125))
+    dt = 0.25 * h
+    ev.step(0.0, dt, steps=40)
+    O.evolve(og, op, ref, 0.0, dt, 40)
+    assert field_errors(ev.get(), ref).max() <= STEP_TOL
+
+
+def test_invalid_arguments_launch_nothing(C):
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    g = C.make_grid((16, 16, 16), 0.0625)
+    p = C.make_params()
+    ev = Evolution(g, p)
+    out = torch.empty_like(ev.state)
+    assert C.cosmos_rhs(g, p, ev.state, ev.state, 0.0) == C.COSMOS_EINVAL  # aliasing
+    small = torch.empty(16, dtype=torch.float64, device="cuda")
+    pf = C.make_params(fluid=1)
+    evf = Evolution(g, pf)
+    assert C.cosmos_rhs(g, pf, evf.state, torch.empty_like(evf.state), 0.0, small) == C.COSMOS_EWORKSPACE
+    assert C.cosmos_rk4_stage(g, p, 5, ev.state, ev.state, out, out, 0.0, 0.1) == C.COSMOS_EINVAL
+    assert C.cosmos_init_grid(g, pf, C.make_id(0, A=0.01), evf.state, evf.ws_init) == C.COSMOS_EINVAL
