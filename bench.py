@@ -37,6 +37,22 @@ STATE_FIELDS = 24
 BYTES_PER_POINT_STAGE = [8 * 3 * 24, 8 * 5 * 24, 8 * 5 * 24, 8 * 4 * 24]
 # RK4 combine flops per field per stage (stage 1: 2; 2-3: 4; 4: 3)
 COMBINE_FLOPS = [2, 4, 4, 3]
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one stage-1 launch
+# of the vacuum stage kernel, from the committed ncu capture of the 96^3 case
+# (3.027 + 7.288 GB), and the hash of the kernel sources it was taken on.  Reported scaled to the bench
+# grid by points; null when the kernel sources differ from the profiled ones.
+NCU_TRAFFIC = {"sources_sha256_16": "c1e137dd9707b898", "grid": 96, "bytes_per_launch": 10.314704e9}
+KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_vac.cu", "generated/bssn_algebra.cuh"]
+
+
+def kernel_sources_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2606_02053_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -105,7 +121,7 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    res = cpu_baseline_sample(args.grid, planes=4, repeats=max(1, args.steps))
+    res = cpu_baseline_sample(args.grid, planes=16, repeats=max(1, args.steps))
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -261,8 +277,12 @@ def main():
         flops_launch = pts * (rhs_flops + COMBINE_FLOPS[dom] * STATE_FIELDS)
         achieved = flops_launch / avg_stage[dom] / 1e12
         peak = fp64_peak / 1e12
+        traffic = None
+        if kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"]:
+            traffic = NCU_TRAFFIC["bytes_per_launch"] * (n / NCU_TRAFFIC["grid"]) ** 3
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"stage_kernel<T_vac, stage {dom + 1}>",
+                "traffic": traffic, "traffic_note": "bytes per launch, ncu at 96^3 scaled by points",
+                "kernel": f"stage_kernel<T_vac, stage {dom + 1}>",
                 "peak_source": "FP64 DFMA throughput measured in this run (cosmos_probe_fp64); nominal 1.25",
                 "algorithmic_flops_per_point_rhs": rhs_flops,
                 "hbm_GBps_algorithmic": pts * BYTES_PER_POINT_STAGE[dom] / avg_stage[dom] / 1e9}

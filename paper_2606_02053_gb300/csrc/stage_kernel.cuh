@@ -11,6 +11,10 @@
 
 #include "common.cuh"
 
+#ifndef COSMOS_STAGE_MIN_BLOCKS
+#define COSMOS_STAGE_MIN_BLOCKS 3  // resident 128-thread blocks per SM the register budget is sized for
+#endif
+
 namespace cosmos {
 
 template <int D>
@@ -62,12 +66,15 @@ __device__ __forceinline__ double fdmix(const double* __restrict__ F, const Nbr&
 }
 
 // rhs + sigma/64 sum_d (1/h_d) [ (f+3 + f-3) - 6 (f+2 + f-2) + 15 (f+1 + f-1) - 20 f0 ]
+// grouped as (s3 - s2) - 5 (s2 - s1) + 10 (s1 - 2 f0), s_k = f+k + f-k: the same
+// coefficients, and every bracket is exactly zero when the neighbours equal f0.
 template <int D>
 __device__ __forceinline__ double ko_dir(const double* __restrict__ F, const Nbr& n, double f0) {
   const double s1 = ldg(F, disp<D>(n, 1)) + ldg(F, disp<D>(n, -1));
   const double s2 = ldg(F, disp<D>(n, 2)) + ldg(F, disp<D>(n, -2));
   const double s3 = ldg(F, disp<D>(n, 3)) + ldg(F, disp<D>(n, -3));
-  return (s3 - 6.0 * s2) + (15.0 * s1 - 20.0 * f0);
+  const double t = fma(-2.0, f0, s1);
+  return fma(10.0, t, fma(-5.0, s2 - s1, s3 - s2));
 }
 
 __device__ __forceinline__ double ko_add(const double* __restrict__ F, const Nbr& n, const Coef& c, double f0,
@@ -108,7 +115,7 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
 }
 
 template <class T, int MODE>
-__global__ void __launch_bounds__(BX* BY, 2) stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS) stage_kernel(const StageArgs a) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
