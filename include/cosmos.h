@@ -151,6 +151,32 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
 int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
                        double norms_host[8], void* ws, size_t ws_bytes, void* stream);
 
+/* cosmos_constraints without a workspace argument, for callers that cannot
+ * allocate device memory: code that runs while a stream is being captured
+ * into a CUDA graph, inside host callbacks, or in a host application whose
+ * memory pool forbids cudaMalloc/cudaFree (and the device-wide
+ * synchronisation they can imply) once it is running.  The paper has no
+ * counterpart; this is a library-usage variant of cosmos_constraints with the
+ * same outputs and the same synchronous behaviour.
+ *
+ * Scratch: one static device array of 2^21 doubles (16 MiB) inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  It must hold (fluid on: 4 * cosmos_field_stride, rounded up to 32
+ * doubles) + 8 * (number of 32 x 4 thread blocks over the grid, rounded up to
+ * 32) + 8 doubles; larger grids return COSMOS_EWORKSPACE before anything is
+ * launched (e.g. 256^3 vacuum fits; with the fluid on, up to about 80^3).
+ * The first call made with a device current resolves the array's device
+ * address for that device (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ * Every call overwrites all the scratch it reads, so no state carries over
+ * between calls, but all calls share the one array: calls that can overlap
+ * on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  On COSMOS_ECUDA the CUDA runtime's
+ * cudaGetLastError() gives the error. */
+int cosmos_constraints_noalloc(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
+                               double norms_host[8], void* stream);
+
 /* Measured FP64 fused-multiply-add throughput of the current device, in
  * flop/s (2 flop per DFMA), from a timed launch of independent DFMA chains
  * on every SM.  Synchronous; allocates nothing (writes one double per thread

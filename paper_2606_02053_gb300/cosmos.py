@@ -64,6 +64,7 @@ _SIGS = {
     "cosmos_rk4_step": ([_G, _PP, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
+    "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_probe_fp64": ([_P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_last_cuda_error": ([], ctypes.c_int),
     "cosmos_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -159,6 +160,12 @@ def cosmos_constraints(g, p, state, ham_mom, norms_out, ws=None, stream=None) ->
     w, nb = _ws(ws)
     return lib().cosmos_constraints(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(ham_mom), norms_out, w, nb,
                                     _stream(stream))
+
+
+def cosmos_constraints_noalloc(g, p, state, ham_mom, norms_out, stream=None) -> int:
+    """cosmos_constraints with the library's static scratch (no workspace argument)."""
+    return lib().cosmos_constraints_noalloc(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(ham_mom), norms_out,
+                                            _stream(stream))
 
 
 def cosmos_probe_fp64(scratch, stream=None) -> float:
