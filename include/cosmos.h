@@ -151,6 +151,56 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
 int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
                        double norms_host[8], void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched evolution of many independent grids (a threshold scan: one
+ * instance per amplitude or shape of the initial perturbation, grids of
+ * uneven sizes, each with its own dt).  All instances share one
+ * cosmos_params.  Per RK4 stage, one persistent launch (plus the two fluid
+ * passes when the fluid is on) sweeps a flat work list holding every point
+ * of every instance, so small or uneven grids leave no SM idle; a run of
+ * several steps can be captured once into a CUDA graph and replayed.
+ * ------------------------------------------------------------------------ */
+typedef struct cosmos_batch_s* cosmos_batch;
+
+typedef struct {
+  int mapping;       /* 0: 2D tiles of block_x x block_y points in one z-plane;
+                        1: runs of block_x * block_y consecutive points */
+  int block_x, block_y; /* block_x * block_y must be 128 */
+  int blocks_per_sm; /* persistent grid = blocks_per_sm * SM count, 1..3 */
+} cosmos_batch_tuning;
+
+/* Device workspace for a batch: per instance two stage buffers, the RK4
+ * accumulator and the fluid buffers, plus the work list and the per-step
+ * K_ref table for up to max_steps steps. */
+size_t cosmos_batch_workspace_bytes(int n, const cosmos_grid* grids, const cosmos_params* p, int max_steps);
+
+/* Build a plan (host memory, freed by cosmos_batch_free) over n instances:
+ * grids[i], time step dt[i], start time t0[i] and device state states[i]
+ * (layout of include/cosmos.h).  Copies the work list and tables into `ws`
+ * (synchronous).  tuning = NULL picks 2D tiles 32 x 4, 3 blocks per SM. */
+int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, const double* dt, const double* t0,
+                      double* const* states, int max_steps, const cosmos_batch_tuning* tuning, void* ws,
+                      size_t ws_bytes, cosmos_batch* plan_out);
+
+/* Change the work-list mapping / launch shape (synchronous; drops any
+ * captured graph). */
+int cosmos_batch_set_tuning(cosmos_batch plan, const cosmos_batch_tuning* tuning);
+
+/* Advance every instance by `steps` RK4 steps, global step indices
+ * first_step .. first_step + steps - 1 (<= max_steps).  use_graph = 1
+ * captures the whole sequence into a CUDA graph on the first call with these
+ * (first_step, steps) and replays it afterwards; it needs a non-NULL stream.
+ * Asynchronous on `stream`. */
+int cosmos_batch_run(cosmos_batch plan, int first_step, int steps, int use_graph, void* stream);
+
+/* Mean time of one RK4 stage-1 pass over the whole batch with the current
+ * tuning, over `reps` passes, in milliseconds (CUDA events; synchronous).
+ * Stage 1 writes only the stage buffers and accumulators, so the instance
+ * states are unchanged.  Used by the autotuner. */
+int cosmos_batch_time_stage(cosmos_batch plan, int reps, double* ms_out, void* stream);
+
+void cosmos_batch_free(cosmos_batch plan);
+
 /* cosmos_constraints without a workspace argument, for callers that cannot
  * allocate device memory: code that runs while a stream is being captured
  * into a CUDA graph, inside host callbacks, or in a host application whose

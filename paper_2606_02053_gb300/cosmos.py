@@ -42,6 +42,11 @@ class cosmos_id(ctypes.Structure):
                 ("t", ctypes.c_double)]
 
 
+class cosmos_batch_tuning(ctypes.Structure):
+    _fields_ = [("mapping", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int)]
+
+
 class CosmosError(RuntimeError):
     pass
 
@@ -66,6 +71,14 @@ _SIGS = {
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_probe_fp64": ([_P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_batch_workspace_bytes": ([ctypes.c_int, _G, _PP, ctypes.c_int], ctypes.c_size_t),
+    "cosmos_batch_plan": ([ctypes.c_int, _G, _PP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(cosmos_batch_tuning), _P, _S,
+                           ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "cosmos_batch_set_tuning": ([_P, ctypes.POINTER(cosmos_batch_tuning)], ctypes.c_int),
+    "cosmos_batch_run": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "cosmos_batch_time_stage": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_batch_free": ([_P], None),
     "cosmos_last_cuda_error": ([], ctypes.c_int),
     "cosmos_strerror": ([ctypes.c_int], ctypes.c_char_p),
 }
@@ -172,6 +185,43 @@ def cosmos_probe_fp64(scratch, stream=None) -> float:
     out = ctypes.c_double(0.0)
     check(lib().cosmos_probe_fp64(_ptr(scratch), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+def cosmos_batch_workspace_bytes(grids, p, max_steps) -> int:
+    arr = (cosmos_grid * len(grids))(*grids)
+    return lib().cosmos_batch_workspace_bytes(len(grids), arr, ctypes.byref(p), int(max_steps))
+
+
+def cosmos_batch_plan(grids, p, dts, t0s, states, max_steps, tuning, ws):
+    """Returns (code, plan handle as c_void_p)."""
+    n = len(grids)
+    arr = (cosmos_grid * n)(*grids)
+    dt = (ctypes.c_double * n)(*dts)
+    t0 = (ctypes.c_double * n)(*t0s)
+    st = (ctypes.c_void_p * n)(*[s.data_ptr() for s in states])
+    plan = ctypes.c_void_p()
+    w, nb = _ws(ws)
+    code = lib().cosmos_batch_plan(n, arr, ctypes.byref(p), dt, t0, st, int(max_steps),
+                                   None if tuning is None else ctypes.byref(tuning), w, nb, ctypes.byref(plan))
+    return code, plan
+
+
+def cosmos_batch_set_tuning(plan, tuning) -> int:
+    return lib().cosmos_batch_set_tuning(plan, ctypes.byref(tuning))
+
+
+def cosmos_batch_run(plan, first_step, steps, use_graph, stream=None) -> int:
+    return lib().cosmos_batch_run(plan, int(first_step), int(steps), int(use_graph), _stream(stream))
+
+
+def cosmos_batch_time_stage(plan, reps, stream=None):
+    ms = ctypes.c_double(0.0)
+    code = lib().cosmos_batch_time_stage(plan, int(reps), ctypes.byref(ms), _stream(stream))
+    return code, ms.value
+
+
+def cosmos_batch_free(plan) -> None:
+    lib().cosmos_batch_free(plan)
 
 
 # ---- convenience constructors (plain data) -----------------------------------

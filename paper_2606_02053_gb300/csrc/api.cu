@@ -50,12 +50,12 @@ DevGrid make_devgrid(const cosmos_grid* g) {
   return d;
 }
 
-static double K_ref(const cosmos_params* p, double t) {
+double K_ref(const cosmos_params* p, double t) {
   if (p->H0 == 0.0) return 0.0;
   return -3.0 * p->H0 / (1.0 + 1.5 * (1.0 + p->w) * p->H0 * (t - p->t0));
 }
 
-static AlgebraParams algebra_params(const cosmos_params* p, double t) {
+AlgebraParams algebra_params(const cosmos_params* p, double t) {
   AlgebraParams a;
   a.eta = p->eta;
   a.Kref = K_ref(p, t);
@@ -75,7 +75,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-static int validate(const cosmos_grid* g, const cosmos_params* p) {
+int validate(const cosmos_grid* g, const cosmos_params* p) {
   if (!g || !p) return COSMOS_EINVAL;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->pitch < g->nx) return COSMOS_EINVAL;
   if (g->nz > 65535 || (g->ny + BY - 1) / BY > 65535) return COSMOS_EINVAL;

@@ -1,0 +1,335 @@
+// Batched evolution of many independent grids (threshold scan): plan, run
+// (optionally as one captured CUDA graph) and the stage timing used by the
+// autotuner.  Declared in include/cosmos.h.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cosmos {
+
+static size_t al256(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
+static bool tuning_ok(const cosmos_batch_tuning* t) {
+  if (!t) return false;
+  if (t->mapping != BATCH_MAP_TILE2D && t->mapping != BATCH_MAP_LINEAR) return false;
+  if (t->block_x < 1 || t->block_y < 1 || t->block_x * t->block_y != BX * BY) return false;
+  return t->blocks_per_sm >= 1 && t->blocks_per_sm <= 3;
+}
+
+// Work items for a tuning; the 2D mapping needs block_x * block_y = 128 threads.
+static long count_tiles(const cosmos_grid& g, const cosmos_batch_tuning& t) {
+  if (t.mapping == BATCH_MAP_LINEAR) {
+    const long npts = (long)g.nx * g.ny * g.nz;
+    return (npts + BX * BY - 1) / (BX * BY);
+  }
+  return (long)((g.nx + t.block_x - 1) / t.block_x) * ((g.ny + t.block_y - 1) / t.block_y) * g.nz;
+}
+
+// Largest work list over every tuning cosmos_batch_set_tuning accepts.
+static long max_tiles(const cosmos_grid& g) {
+  long m = 0;
+  for (int bx = 1; bx <= BX * BY; bx *= 2) {
+    cosmos_batch_tuning t = {BATCH_MAP_TILE2D, bx, BX * BY / bx, 1};
+    m = std::max(m, count_tiles(g, t));
+  }
+  cosmos_batch_tuning lin = {BATCH_MAP_LINEAR, BX, BY, 1};
+  return std::max(m, count_tiles(g, lin));
+}
+
+struct BatchLayout {
+  std::vector<size_t> A, B, acc, prim, flux;  // per instance, in doubles from ws
+  size_t args, tiles, kref;                   // byte offsets
+  size_t total;
+};
+
+static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_params* p, int max_steps) {
+  BatchLayout L;
+  const int nf = 24 + 4 * p->fluid + 2 * p->scalar;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += al256(bytes);
+    return o;
+  };
+  long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t fs = (size_t)grids[i].pitch * grids[i].ny * grids[i].nz;
+    L.A.push_back(take(nf * fs * 8) / 8);
+    L.B.push_back(take(nf * fs * 8) / 8);
+    L.acc.push_back(take(nf * fs * 8) / 8);
+    L.prim.push_back(p->fluid ? take(4 * fs * 8) / 8 : 0);
+    L.flux.push_back(p->fluid ? take(12 * fs * 8) / 8 : 0);
+    tiles += max_tiles(grids[i]);
+  }
+  L.args = take(sizeof(StageArgs) * 4 * (size_t)n);
+  L.tiles = take(sizeof(BatchTile) * (size_t)tiles);
+  L.kref = take(sizeof(double) * (size_t)max_steps * 4 * n);
+  L.total = off;
+  return L;
+}
+
+}  // namespace cosmos
+
+using namespace cosmos;
+
+struct cosmos_batch_s {
+  int n = 0;
+  cosmos_params p;
+  std::vector<cosmos_grid> grids;
+  int max_steps = 0;
+  cosmos_batch_tuning tune;
+  int sms = 0;
+  char* ws = nullptr;
+  BatchLayout L;
+  long ntiles = 0;
+  StageArgs* d_args = nullptr;  // [4][n]
+  BatchTile* d_tiles = nullptr;
+  double* d_kref = nullptr;     // [max_steps][4][n]
+  cudaGraphExec_t gexec = nullptr;
+  int g_first = -1, g_steps = -1;
+  cudaStream_t g_stream = nullptr;
+};
+
+static void drop_graph(cosmos_batch b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->g_first = b->g_steps = -1;
+}
+
+static int upload_tiles(cosmos_batch b) {
+  std::vector<BatchTile> tiles;
+  const int tpb = BX * BY;
+  for (int i = 0; i < b->n; ++i) {
+    const cosmos_grid& g = b->grids[i];
+    if (b->tune.mapping == BATCH_MAP_LINEAR) {
+      const long npts = (long)g.nx * g.ny * g.nz;
+      for (long s = 0; s < npts; s += tpb) tiles.push_back(BatchTile{i, (int)s, 0, 0});
+    } else {
+      const int tx = (g.nx + b->tune.block_x - 1) / b->tune.block_x;
+      const int ty = (g.ny + b->tune.block_y - 1) / b->tune.block_y;
+      for (int k = 0; k < g.nz; ++k)
+        for (int by = 0; by < ty; ++by)
+          for (int bx = 0; bx < tx; ++bx) tiles.push_back(BatchTile{i, bx, by, k});
+    }
+  }
+  // interleave instances so that consecutive work items (taken by different
+  // persistent blocks in the same round) come from different grids
+  std::vector<BatchTile> mixed;
+  mixed.reserve(tiles.size());
+  {
+    std::vector<size_t> start(b->n + 1, 0);
+    for (auto& t : tiles) start[t.inst + 1]++;
+    for (int i = 0; i < b->n; ++i) start[i + 1] += start[i];
+    std::vector<size_t> pos(start.begin(), start.end() - 1);
+    bool any = true;
+    while (any) {
+      any = false;
+      for (int i = 0; i < b->n; ++i)
+        if (pos[i] < start[i + 1]) {
+          mixed.push_back(tiles[pos[i]++]);
+          any = true;
+        }
+    }
+  }
+  b->ntiles = (long)mixed.size();
+  if (cudaMemcpy(b->d_tiles, mixed.data(), sizeof(BatchTile) * mixed.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return COSMOS_ECUDA;
+  return COSMOS_OK;
+}
+
+extern "C" {
+
+size_t cosmos_batch_workspace_bytes(int n, const cosmos_grid* grids, const cosmos_params* p, int max_steps) {
+  if (n < 1 || !grids || !p || max_steps < 1) return 0;
+  for (int i = 0; i < n; ++i)
+    if (validate(&grids[i], p) != COSMOS_OK) return 0;
+  return batch_layout(n, grids, p, max_steps).total;
+}
+
+int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, const double* dt, const double* t0,
+                      double* const* states, int max_steps, const cosmos_batch_tuning* tuning, void* ws,
+                      size_t ws_bytes, cosmos_batch* plan_out) {
+  if (n < 1 || !grids || !p || !dt || !t0 || !states || max_steps < 1 || !plan_out) return COSMOS_EINVAL;
+  *plan_out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (validate(&grids[i], p) != COSMOS_OK) return COSMOS_EINVAL;
+    if (!states[i] || !(dt[i] > 0.0)) return COSMOS_EINVAL;
+    if ((uintptr_t)states[i] & 15u) return COSMOS_EALIGN;
+  }
+  cosmos_batch_tuning def = {BATCH_MAP_TILE2D, BX, BY, 3};
+  if (tuning && !tuning_ok(tuning)) return COSMOS_EINVAL;
+  const BatchLayout L = batch_layout(n, grids, p, max_steps);
+  if (!ws) return COSMOS_EINVAL;
+  if (ws_bytes < L.total) return COSMOS_EWORKSPACE;
+  if ((uintptr_t)ws & 255u) return COSMOS_EALIGN;
+
+  cosmos_batch b = new cosmos_batch_s();
+  b->n = n;
+  b->p = *p;
+  b->grids.assign(grids, grids + n);
+  b->max_steps = max_steps;
+  b->tune = tuning ? *tuning : def;
+  b->ws = (char*)ws;
+  b->L = L;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  double* wsd = (double*)ws;
+  b->d_args = (StageArgs*)(b->ws + L.args);
+  b->d_tiles = (BatchTile*)(b->ws + L.tiles);
+  b->d_kref = (double*)(b->ws + L.kref);
+
+  // per-stage, per-instance arguments (same fields as the single-grid stages)
+  std::vector<StageArgs> args(4 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    double* A = wsd + L.A[i];
+    double* B = wsd + L.B[i];
+    double* acc = wsd + L.acc[i];
+    double* U = states[i];
+    const double* Us[4] = {U, A, B, A};
+    double* outs[4] = {A, B, A, nullptr};
+    const double cdt[4] = {0.5 * dt[i], 0.5 * dt[i], dt[i], dt[i] / 6.0};
+    for (int s = 0; s < 4; ++s) {
+      StageArgs& a = args[(size_t)s * n + i];
+      memset(&a, 0, sizeof(a));
+      a.g = make_devgrid(&grids[i]);
+      a.c = make_coef(&grids[i], p->ko_sigma);
+      a.ap = algebra_params(p, t0[i]);
+      a.U = Us[s];
+      a.U0 = U;
+      a.U0w = U;
+      a.out = outs[s];
+      a.acc = acc;
+      a.cdt = cdt[s];
+      a.bk = 2.0;
+      if (p->fluid) {
+        a.prim = wsd + L.prim[i];
+        a.flux = wsd + L.flux[i];
+      }
+    }
+  }
+  // K_ref at every stage time: t = (t0 + step dt) + c_s dt, c = 0, 1/2, 1/2, 1
+  // (the same sums as cosmos_rk4_step at t0 + step dt)
+  static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
+  std::vector<double> kref((size_t)max_steps * 4 * n);
+  for (int st = 0; st < max_steps; ++st)
+    for (int s = 0; s < 4; ++s)
+      for (int i = 0; i < n; ++i) {
+        const double tn = t0[i] + st * dt[i];
+        const double ts = s == 0 ? tn : (s == 3 ? tn + dt[i] : tn + c_stage[s] * dt[i]);
+        kref[((size_t)st * 4 + s) * n + i] = K_ref(p, ts);
+      }
+  if (cudaMemcpy(b->d_args, args.data(), sizeof(StageArgs) * args.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_kref, kref.data(), sizeof(double) * kref.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    delete b;
+    return COSMOS_ECUDA;
+  }
+  const int e = upload_tiles(b);
+  if (e != COSMOS_OK) {
+    delete b;
+    return e;
+  }
+  *plan_out = b;
+  return COSMOS_OK;
+}
+
+int cosmos_batch_set_tuning(cosmos_batch b, const cosmos_batch_tuning* tuning) {
+  if (!b || !tuning_ok(tuning)) return COSMOS_EINVAL;
+  drop_graph(b);
+  b->tune = *tuning;
+  return upload_tiles(b);
+}
+
+static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStream_t s) {
+  typedef cudaError_t (*L)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
+                           cudaStream_t);
+  L launch = launch_batch_stage_vac;
+  if (b->p.fluid && b->p.scalar)
+    launch = launch_batch_stage_fluid_scalar;
+  else if (b->p.fluid)
+    launch = launch_batch_stage_fluid;
+  else if (b->p.scalar)
+    launch = launch_batch_stage_scalar;
+  const dim3 grid(b->sms * b->tune.blocks_per_sm), block(b->tune.block_x, b->tune.block_y);
+  static const int modes[4] = {MODE_S1, MODE_S23, MODE_S23, MODE_S4};
+  for (int st = first_step; st < first_step + steps; ++st)
+    for (int stage = 0; stage < 4; ++stage) {
+      const StageArgs* args = b->d_args + (size_t)stage * b->n;
+      if (b->p.fluid &&
+          launch_batch_fluid(args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
+        return COSMOS_ECUDA;
+      const double* kref = b->d_kref + ((size_t)st * 4 + stage) * b->n;
+      if (launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s) != cudaSuccess)
+        return COSMOS_ECUDA;
+    }
+  return COSMOS_OK;
+}
+
+int cosmos_batch_run(cosmos_batch b, int first_step, int steps, int use_graph, void* stream) {
+  if (!b || first_step < 0 || steps < 0 || first_step + steps > b->max_steps) return COSMOS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph) return batch_launch_steps(b, first_step, steps, s);
+  if (!s) return COSMOS_EINVAL;  // the legacy default stream cannot be captured
+  if (!(b->gexec && b->g_first == first_step && b->g_steps == steps && b->g_stream == s)) {
+    drop_graph(b);
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return COSMOS_ECUDA;
+    const int e = batch_launch_steps(b, first_step, steps, s);
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (e != COSMOS_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return e != COSMOS_OK ? e : COSMOS_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      b->gexec = nullptr;
+      return COSMOS_ECUDA;
+    }
+    b->g_first = first_step;
+    b->g_steps = steps;
+    b->g_stream = s;
+  }
+  return cudaGraphLaunch(b->gexec, s) == cudaSuccess ? COSMOS_OK : COSMOS_ECUDA;
+}
+
+int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stream) {
+  if (!b || reps < 1 || !ms_out) return COSMOS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  typedef cudaError_t (*L)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
+                           cudaStream_t);
+  L launch = b->p.fluid ? (b->p.scalar ? launch_batch_stage_fluid_scalar : launch_batch_stage_fluid)
+                        : (b->p.scalar ? launch_batch_stage_scalar : launch_batch_stage_vac);
+  const dim3 grid(b->sms * b->tune.blocks_per_sm), block(b->tune.block_x, b->tune.block_y);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return COSMOS_ECUDA;
+  int rc = COSMOS_OK;
+  for (int r = -1; r < reps && rc == COSMOS_OK; ++r) {  // r = -1: warm-up
+    if (r == 0) cudaEventRecord(e0, s);
+    if (b->p.fluid &&
+        launch_batch_fluid(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
+      rc = COSMOS_ECUDA;
+    if (rc == COSMOS_OK &&
+        launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s) != cudaSuccess)
+      rc = COSMOS_ECUDA;
+  }
+  cudaEventRecord(e1, s);
+  if (cudaEventSynchronize(e1) != cudaSuccess) rc = COSMOS_ECUDA;
+  float ms = 0.f;
+  if (rc == COSMOS_OK) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return rc;
+}
+
+void cosmos_batch_free(cosmos_batch b) {
+  if (!b) return;
+  drop_graph(b);
+  delete b;
+}
+
+}  // extern "C"

@@ -64,6 +64,9 @@ struct Coef {
 
 Coef make_coef(const cosmos_grid* g, double sigma);
 DevGrid make_devgrid(const cosmos_grid* g);
+double K_ref(const cosmos_params* p, double t);                 // background trace at time t
+AlgebraParams algebra_params(const cosmos_params* p, double t); // runtime parameters of the algebra
+int validate(const cosmos_grid* g, const cosmos_params* p);     // COSMOS_OK or COSMOS_EINVAL
 
 // RK4 stage modes of the fused kernel
 enum StageMode { MODE_RHS = 0, MODE_S1 = 1, MODE_S23 = 2, MODE_S4 = 3 };
@@ -83,6 +86,13 @@ struct StageArgs {
   double bk;                       // accumulator weight (2 for stages 2, 3)
 };
 
+// One work item of a batch: instance `inst`; for 2D tiles (a, b, c) = (block
+// column, block row, z-plane), for linear runs a = first point index.
+struct BatchTile {
+  int inst, a, b, c;
+};
+enum BatchMapping { BATCH_MAP_TILE2D = 0, BATCH_MAP_LINEAR = 1 };
+
 struct ConstraintArgs {
   DevGrid g;
   Coef c;
@@ -98,6 +108,16 @@ cudaError_t launch_stage_vac(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_scalar(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid_scalar(const StageArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_batch_stage_vac(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
+                                   cudaStream_t);
+cudaError_t launch_batch_stage_fluid(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
+                                     cudaStream_t);
+cudaError_t launch_batch_stage_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
+                                      cudaStream_t);
+cudaError_t launch_batch_stage_fluid_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
+                                            dim3, cudaStream_t);
+cudaError_t launch_batch_fluid(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping, double w,
+                               dim3 grid, dim3 block, cudaStream_t s);
 cudaError_t launch_constraints_vac(const ConstraintArgs& a, cudaStream_t s);
 cudaError_t launch_constraints_fluid(const ConstraintArgs& a, cudaStream_t s);
 cudaError_t launch_constraints_scalar(const ConstraintArgs& a, cudaStream_t s);

@@ -6,12 +6,8 @@
 
 namespace cosmos {
 
-__global__ void __launch_bounds__(BX* BY) prim_kernel(const DevGrid g, const double* __restrict__ U,
-                                                      double* __restrict__ prim, const FluidParams fp) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return;
+__device__ __forceinline__ void prim_point(const DevGrid& g, const double* __restrict__ U, double* __restrict__ prim,
+                                           const FluidParams& fp, int i, int j, int k) {
   const long c = ((long)k * g.ny + j) * g.pitch + i;
   const long fs = g.fstride;
   double in[11];
@@ -24,6 +20,15 @@ __global__ void __launch_bounds__(BX* BY) prim_kernel(const DevGrid g, const dou
   fluid_prim(in, out, fp);
 #pragma unroll
   for (int m = 0; m < 4; ++m) prim[m * fs + c] = out[m];
+}
+
+__global__ void __launch_bounds__(BX* BY) prim_kernel(const DevGrid g, const double* __restrict__ U,
+                                                      double* __restrict__ prim, const FluidParams fp) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  prim_point(g, U, prim, fp, i, j, k);
 }
 
 template <int D>
@@ -54,6 +59,15 @@ __device__ __forceinline__ void face(const double* __restrict__ U, const double*
   for (int m = 0; m < 4; ++m) H[(4 * D + m) * fs + n.c] = out[m];
 }
 
+__device__ __forceinline__ void flux_point(const DevGrid& g, const double* __restrict__ U,
+                                           const double* __restrict__ prim, double* __restrict__ H,
+                                           const FluidParams& fp, int i, int j, int k) {
+  const Nbr n = make_nbr(g, i, j, k);
+  face<0>(U, prim, n, g.fstride, fp, H);
+  face<1>(U, prim, n, g.fstride, fp, H);
+  face<2>(U, prim, n, g.fstride, fp, H);
+}
+
 __global__ void __launch_bounds__(BX* BY) flux_kernel(const DevGrid g, const double* __restrict__ U,
                                                       const double* __restrict__ prim, double* __restrict__ H,
                                                       const FluidParams fp) {
@@ -61,10 +75,31 @@ __global__ void __launch_bounds__(BX* BY) flux_kernel(const DevGrid g, const dou
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
-  const Nbr n = make_nbr(g, i, j, k);
-  face<0>(U, prim, n, g.fstride, fp, H);
-  face<1>(U, prim, n, g.fstride, fp, H);
-  face<2>(U, prim, n, g.fstride, fp, H);
+  flux_point(g, U, prim, H, fp, i, j, k);
+}
+
+// Batched passes: blocks stride over the flat work list of every instance
+// (stage input args[inst].U, outputs into that instance's prim / flux buffers).
+__global__ void __launch_bounds__(BX* BY) batch_prim_kernel(const StageArgs* __restrict__ args,
+                                                            const BatchTile* __restrict__ tiles, long ntiles,
+                                                            int mapping, const FluidParams fp) {
+  for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+    const BatchTile t = tiles[w];
+    const StageArgs& a = args[t.inst];
+    int i, j, k;
+    if (batch_point(t, a.g, mapping, i, j, k)) prim_point(a.g, a.U, const_cast<double*>(a.prim), fp, i, j, k);
+  }
+}
+
+__global__ void __launch_bounds__(BX* BY) batch_flux_kernel(const StageArgs* __restrict__ args,
+                                                            const BatchTile* __restrict__ tiles, long ntiles,
+                                                            int mapping, const FluidParams fp) {
+  for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+    const BatchTile t = tiles[w];
+    const StageArgs& a = args[t.inst];
+    int i, j, k;
+    if (batch_point(t, a.g, mapping, i, j, k)) flux_point(a.g, a.U, a.prim, const_cast<double*>(a.flux), fp, i, j, k);
+  }
 }
 
 static FluidParams fluid_params(double w) {
@@ -76,6 +111,15 @@ static FluidParams fluid_params(double w) {
 
 cudaError_t launch_fluid_prim(const DevGrid& g, const double* U, double* prim, double w, cudaStream_t s) {
   prim_kernel<<<point_grid(g), dim3(BX, BY), 0, s>>>(g, U, prim, fluid_params(w));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_fluid(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping, double w,
+                               dim3 grid, dim3 block, cudaStream_t s) {
+  batch_prim_kernel<<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, fluid_params(w));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_flux_kernel<<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, fluid_params(w));
   return cudaGetLastError();
 }
 

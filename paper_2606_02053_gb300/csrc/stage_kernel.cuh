@@ -114,18 +114,15 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
   if constexpr (T::FLUID) in[T::NIN - 1] = ldg(prim, n.c);
 }
 
+// RHS + stage combine at one grid point (i, j, k) of one grid.
 template <class T, int MODE>
-__global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS) stage_kernel(const StageArgs a) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= a.g.nx || j >= a.g.ny) return;
+__device__ __forceinline__ void stage_point(const StageArgs& a, const AlgebraParams& ap, int i, int j, int k) {
   const Nbr n = make_nbr(a.g, i, j, k);
   const long fs = a.g.fstride;
   double in[T::NIN];
   gather<T>(a.U, a.prim, n, a.c, fs, in);
   double out[T::NF];
-  T::rhs(in, out, a.ap);
+  T::rhs(in, out, ap);
 #pragma unroll
   for (int f = 0; f < T::NF; ++f) {
     double r = out[f];
@@ -149,6 +146,52 @@ __global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS) stage_kernel(
     } else {
       a.U0w[o] = fma(a.cdt, a.acc[o] + r, a.U0w[o]);
     }
+  }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS) stage_kernel(const StageArgs a) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= a.g.nx || j >= a.g.ny) return;
+  stage_point<T, MODE>(a, a.ap, i, j, k);
+}
+
+// Point (i, j, k) of work item `t` (thread `lane` of the block) of a batch:
+// 2D tiles of blockDim.x x blockDim.y points in one z-plane, or runs of
+// blockDim.x * blockDim.y consecutive points in memory order.  Returns false
+// for a thread past the grid edge.
+__device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g, int mapping, int& i, int& j,
+                                            int& k) {
+  if (mapping == BATCH_MAP_TILE2D) {
+    i = t.a * blockDim.x + threadIdx.x;
+    j = t.b * blockDim.y + threadIdx.y;
+    k = t.c;
+    return i < g.nx && j < g.ny;
+  }
+  const long p = (long)t.a + threadIdx.y * blockDim.x + threadIdx.x;
+  const long npts = (long)g.nx * g.ny * g.nz;
+  if (p >= npts) return false;
+  i = (int)(p % g.nx);
+  j = (int)((p / g.nx) % g.ny);
+  k = (int)(p / ((long)g.nx * g.ny));
+  return true;
+}
+
+// Persistent batched stage kernel: blocks stride over the flat work list of
+// all instances; instance `inst` uses args[inst] with K_ref taken from kref.
+template <class T, int MODE>
+__global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS)
+    batch_stage_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles,
+                       int mapping, const double* __restrict__ kref) {
+  for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+    const BatchTile t = tiles[w];
+    const StageArgs& a = args[t.inst];
+    AlgebraParams ap = a.ap;
+    ap.Kref = kref[t.inst];
+    int i, j, k;
+    if (batch_point(t, a.g, mapping, i, j, k)) stage_point<T, MODE>(a, ap, i, j, k);
   }
 }
 
@@ -229,6 +272,21 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
       case MODE_S1: stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(a); break;                          \
       case MODE_S23: stage_kernel<T_##NAME, MODE_S23><<<grid, block, 0, s>>>(a); break;                        \
       default: stage_kernel<T_##NAME, MODE_S4><<<grid, block, 0, s>>>(a); break;                               \
+    }                                                                                                           \
+    return cudaGetLastError();                                                                                  \
+  }                                                                                                             \
+  cudaError_t launch_batch_stage_##NAME(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping,  \
+                                        const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s) {    \
+    switch (mode) {                                                                                             \
+      case MODE_S1:                                                                                             \
+        batch_stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \
+        break;                                                                                                  \
+      case MODE_S23:                                                                                            \
+        batch_stage_kernel<T_##NAME, MODE_S23><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);      \
+        break;                                                                                                  \
+      default:                                                                                                  \
+        batch_stage_kernel<T_##NAME, MODE_S4><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \
+        break;                                                                                                  \
     }                                                                                                           \
     return cudaGetLastError();                                                                                  \
   }                                                                                                             \
