@@ -17,6 +17,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   constraints : autodiff ADM constraints (4th-order convergence), gauge wave.
   init        : gauge-wave closed form; FLRW + zeta gives H = 0 (discrete).
   flop_count  : counts only; no physics.
+  rhs_vjp / adjoint_step : tape reverse mode of rhs / rk4_step; pinned by
+      finite-difference dot-product tests against the (pinned) forward map.
 """
 from __future__ import annotations
 
@@ -68,6 +70,7 @@ def lib():
         L.oracle_constraints.argtypes = [_I, _D, _D, _D, _D, _D, _D]
         L.oracle_init.argtypes = [_I, _D, _D, _D, _D, _D]
         L.oracle_flop_count.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
+        L.oracle_rhs_vjp.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D, _D]
         _lib = L
     return _lib
 
@@ -177,6 +180,50 @@ def init(g: OGrid, params, idarr):
     n, h, x0 = g.c()
     lib().oracle_init(n, h, x0, _dp(params), _dp(np.asarray(idarr, dtype=np.float64)), _dp(state))
     return state
+
+
+def rhs_vjp(g: OGrid, params, state, w, t=0.0):
+    """(dF/dU)^T w by a tape over the whole right-hand side (tiny grids only)."""
+    _check_state(g, params, state)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    assert w.shape == state.shape
+    out = np.empty_like(state)
+    n, h, x0 = g.c()
+    lib().oracle_rhs_vjp(n, h, x0, _dp(params), _dp(state), float(t), _dp(w), _dp(out))
+    return out
+
+
+def rk4_stages(g: OGrid, params, state, t, dt):
+    """Stage states U_1..U_4 of one classic RK4 step (as rk4_step forms them)."""
+    k1 = rhs(g, params, state, t)
+    U2 = state + 0.5 * dt * k1
+    k2 = rhs(g, params, U2, t + 0.5 * dt)
+    U3 = state + 0.5 * dt * k2
+    k3 = rhs(g, params, U3, t + 0.5 * dt)
+    U4 = state + dt * k3
+    return [state, U2, U3, U4]
+
+
+def adjoint_step(g: OGrid, params, state, lam, t, dt):
+    """Reverse of one classic RK4 step U_{n+1} = U_n + dt/6 (k1 + 2 k2 + 2 k3 + k4),
+    k_s = F(U_s, t_s): returns (dU_{n+1}/dU_n)^T lam, stage by stage in reverse:
+    kbar_4 = dt/6 lam, then v_s = (dF/dU at U_s)^T kbar_s feeds lam_n += v_s and
+    kbar_{s-1} = b_{s-1} dt lam + a_{s,s-1} dt v_s (a = 1, 1/2, 1/2)."""
+    U = rk4_stages(g, params, state, t, dt)
+    ts = [t, t + 0.5 * dt, t + 0.5 * dt, t + dt]
+    out = lam.copy()
+    kb = dt / 6.0 * lam
+    v = rhs_vjp(g, params, U[3], kb, ts[3])
+    out += v
+    kb = dt / 3.0 * lam + dt * v
+    v = rhs_vjp(g, params, U[2], kb, ts[2])
+    out += v
+    kb = dt / 3.0 * lam + 0.5 * dt * v
+    v = rhs_vjp(g, params, U[1], kb, ts[1])
+    out += v
+    kb = dt / 6.0 * lam + 0.5 * dt * v
+    out += rhs_vjp(g, params, U[0], kb, ts[0])
+    return out
 
 
 def flop_count(g: OGrid, params, state, t=0.0):

@@ -41,6 +41,7 @@
 #include <cstring>
 #include <vector>
 #include <algorithm>
+#include <type_traits>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -73,6 +74,42 @@ inline double val(Cnt a) { return a.v; }
 inline double val(double a) { return a; }
 using std::sqrt;
 using std::fabs;
+
+/* ------------------------------------------------------------------------ */
+/* Taped scalar for reverse mode: every operation appends a node holding its */
+/* (at most two) parents and the partial derivatives with respect to them.   */
+/* Leaves 0 .. nleaves-1 are the state entries; id -1 marks a constant.      */
+/* ------------------------------------------------------------------------ */
+struct TapeNode { long a, b; double da, db; };
+std::vector<TapeNode> g_tape;  // only touched single-threaded (tiny grids)
+
+struct AD {
+  double v;
+  long id;
+  AD() : v(0), id(-1) {}
+  AD(double x) : v(x), id(-1) {}
+  AD(double x, long i) : v(x), id(i) {}
+};
+inline AD node(double v, long a, double da, long b = -1, double db = 0.0) {
+  if (a < 0 && b < 0) return AD(v);
+  g_tape.push_back(TapeNode{a, b, da, db});
+  return AD(v, (long)g_tape.size() - 1);
+}
+inline AD operator+(AD x, AD y) { return node(x.v + y.v, x.id, 1.0, y.id, 1.0); }
+inline AD operator-(AD x, AD y) { return node(x.v - y.v, x.id, 1.0, y.id, -1.0); }
+inline AD operator*(AD x, AD y) { return node(x.v * y.v, x.id, y.v, y.id, x.v); }
+inline AD operator/(AD x, AD y) { return node(x.v / y.v, x.id, 1.0 / y.v, y.id, -x.v / (y.v * y.v)); }
+inline AD operator-(AD x) { return node(-x.v, x.id, -1.0); }
+inline AD sqrt(AD x) {
+  double r = std::sqrt(x.v);
+  return node(r, x.id, 0.5 / r);
+}
+inline AD fabs(AD x) { return node(std::fabs(x.v), x.id, x.v < 0.0 ? -1.0 : 1.0); }
+inline bool operator<(AD x, AD y) { return x.v < y.v; }
+inline bool operator>(AD x, AD y) { return x.v > y.v; }
+
+template <class R> struct is_ad { static constexpr bool value = false; };
+template <> struct is_ad<AD> { static constexpr bool value = true; };
 
 template <class R> inline R rmax(R a, R b) { return (a < b) ? b : a; }
 template <class R> inline R rmin(R a, R b) { return (b < a) ? b : a; }
@@ -175,11 +212,16 @@ struct Field {
     if (m >= 0 && m < (long)g->wrap[d].size()) return g->wrap[d][m];
     return wrapi(a, g->n[d]);
   }
-  double at(int f, Pt p) const {
+  long index(int f, Pt p) const {
     long i = wrapped(0, p.i[0]), j = wrapped(1, p.i[1]), k = wrapped(2, p.i[2]);
-    return s[(long)f * g->npts() + (k * g->n[1] + j) * g->n[0] + i];
+    return (long)f * g->npts() + (k * g->n[1] + j) * g->n[0] + i;
   }
+  double at(int f, Pt p) const { return s[index(f, p)]; }
 };
+
+/* A state entry as a value of the scalar type (a tape leaf for reverse mode). */
+template <class R> inline R load(const Field& F, int f, Pt p) { return R(F.at(f, p)); }
+template <> inline AD load<AD>(const Field& F, int f, Pt p) { return AD(F.at(f, p), F.index(f, p)); }
 
 inline Pt shift(Pt p, int d, long o) {
   p.i[d] += o;
@@ -200,16 +242,16 @@ inline Pt shift(Pt p, int d, long o) {
 /* ------------------------------------------------------------------------ */
 template <class R>
 R D1(const Field& F, int f, Pt p, int d) {
-  R a = R(F.at(f, shift(p, d, 1))) - R(F.at(f, shift(p, d, -1)));
-  R b = R(F.at(f, shift(p, d, 2))) - R(F.at(f, shift(p, d, -2)));
+  R a = load<R>(F, f, shift(p, d, 1)) - load<R>(F, f, shift(p, d, -1));
+  R b = load<R>(F, f, shift(p, d, 2)) - load<R>(F, f, shift(p, d, -2));
   return (R(8.0) * a - b) / R(12.0 * F.g->h[d]);
 }
 
 template <class R>
 R D2(const Field& F, int f, Pt p, int d) {
-  R f0 = R(F.at(f, p));
-  R s1 = (R(F.at(f, shift(p, d, 1))) - f0) + (R(F.at(f, shift(p, d, -1))) - f0);
-  R s2 = (R(F.at(f, shift(p, d, 2))) - f0) + (R(F.at(f, shift(p, d, -2))) - f0);
+  R f0 = load<R>(F, f, p);
+  R s1 = (load<R>(F, f, shift(p, d, 1)) - f0) + (load<R>(F, f, shift(p, d, -1)) - f0);
+  R s2 = (load<R>(F, f, shift(p, d, 2)) - f0) + (load<R>(F, f, shift(p, d, -2)) - f0);
   return (R(16.0) * s1 - s2) / R(12.0 * F.g->h[d] * F.g->h[d]);
 }
 
@@ -220,19 +262,25 @@ R D2(const Field& F, int f, Pt p, int d) {
  * a grid-wide evaluation that stores first derivatives costs. */
 template <class R>
 R Dmix(const Field& F, int f, Pt p, int a, int b) {
-  R m1 = R(D1<double>(F, f, shift(p, a, 1), b)) - R(D1<double>(F, f, shift(p, a, -1), b));
-  R m2 = R(D1<double>(F, f, shift(p, a, 2), b)) - R(D1<double>(F, f, shift(p, a, -2), b));
-  return (R(8.0) * m1 - m2) / R(12.0 * F.g->h[a]);
+  if constexpr (is_ad<R>::value) {  // reverse mode: the neighbours' derivatives are taped too
+    R m1 = D1<R>(F, f, shift(p, a, 1), b) - D1<R>(F, f, shift(p, a, -1), b);
+    R m2 = D1<R>(F, f, shift(p, a, 2), b) - D1<R>(F, f, shift(p, a, -2), b);
+    return (R(8.0) * m1 - m2) / R(12.0 * F.g->h[a]);
+  } else {
+    R m1 = R(D1<double>(F, f, shift(p, a, 1), b)) - R(D1<double>(F, f, shift(p, a, -1), b));
+    R m2 = R(D1<double>(F, f, shift(p, a, 2), b)) - R(D1<double>(F, f, shift(p, a, -2), b));
+    return (R(8.0) * m1 - m2) / R(12.0 * F.g->h[a]);
+  }
 }
 
 template <class R>
 R KO(const Field& F, int f, Pt p, double sigma) {
-  R f0 = R(F.at(f, p));
+  R f0 = load<R>(F, f, p);
   R sum = R(0.0);
   for (int d = 0; d < 3; ++d) {
-    R s1 = (R(F.at(f, shift(p, d, 1))) - f0) + (R(F.at(f, shift(p, d, -1))) - f0);
-    R s2 = (R(F.at(f, shift(p, d, 2))) - f0) + (R(F.at(f, shift(p, d, -2))) - f0);
-    R s3 = (R(F.at(f, shift(p, d, 3))) - f0) + (R(F.at(f, shift(p, d, -3))) - f0);
+    R s1 = (load<R>(F, f, shift(p, d, 1)) - f0) + (load<R>(F, f, shift(p, d, -1)) - f0);
+    R s2 = (load<R>(F, f, shift(p, d, 2)) - f0) + (load<R>(F, f, shift(p, d, -2)) - f0);
+    R s3 = (load<R>(F, f, shift(p, d, 3)) - f0) + (load<R>(F, f, shift(p, d, -3)) - f0);
     R sd = (s3 - R(6.0) * s2) + R(15.0) * s1;
     sum = sum + sd / R(F.g->h[d]);
   }
@@ -293,18 +341,18 @@ void hess(const Field& F, int f, Pt p, R out[3][3]) {
 
 template <class R>
 void gather(const Field& F, const Params& P, Pt p, Local<R>& L) {
-  L.chi = R(F.at(CHI, p));
-  L.K = R(F.at(TRK, p));
-  L.alpha = R(F.at(ALP, p));
+  L.chi = load<R>(F, CHI, p);
+  L.K = load<R>(F, TRK, p);
+  L.alpha = load<R>(F, ALP, p);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      L.gt[i][j] = R(F.at(GT + sym(i, j), p));
-      L.At[i][j] = R(F.at(AT + sym(i, j), p));
+      L.gt[i][j] = load<R>(F, GT + sym(i, j), p);
+      L.At[i][j] = load<R>(F, AT + sym(i, j), p);
     }
   for (int i = 0; i < 3; ++i) {
-    L.Gt[i] = R(F.at(GAM + i, p));
-    L.beta[i] = R(F.at(BET + i, p));
-    L.B[i] = R(F.at(BB + i, p));
+    L.Gt[i] = load<R>(F, GAM + i, p);
+    L.beta[i] = load<R>(F, BET + i, p);
+    L.B[i] = load<R>(F, BB + i, p);
   }
   grad<R>(F, CHI, p, L.dchi);
   grad<R>(F, TRK, p, L.dK);
@@ -338,16 +386,16 @@ void gather(const Field& F, const Params& P, Pt p, Local<R>& L) {
   }
   if (P.scalar) {
     int s = P.isc();
-    L.phi = R(F.at(s, p));
-    L.Pi = R(F.at(s + 1, p));
+    L.phi = load<R>(F, s, p);
+    L.Pi = load<R>(F, s + 1, p);
     grad<R>(F, s, p, L.dphi);
     grad<R>(F, s + 1, p, L.dPi);
     hess<R>(F, s, p, L.ddphi);
   }
   if (P.fluid) {
     int q = P.ifl();
-    L.tau = R(F.at(q, p));
-    for (int i = 0; i < 3; ++i) L.St[i] = R(F.at(q + 1 + i, p));
+    L.tau = load<R>(F, q, p);
+    for (int i = 0; i < 3; ++i) L.St[i] = load<R>(F, q + 1 + i, p);
   }
 }
 
@@ -736,34 +784,38 @@ R minmod(R a, R b) {
   return R(0.0);
 }
 
-struct Prim { double rho, v[3]; };
+template <class R>
+struct Prim { R rho, v[3]; };
 
-/* Cell-centred primitive variables (plain double: each cell's own recovery
- * is charged once, in matter_sources, by the flop tally). */
-Prim cell_prim(const Field& F, const Params& P, Pt p) {
-  double chi = F.at(CHI, p);
-  double gt[3][3], gtu[3][3];
+/* Cell-centred primitive variables.  In the forward and counting modes they
+ * are evaluated in plain double (each cell's own recovery is charged once, in
+ * matter_sources, by the flop tally); reverse mode tapes them. */
+template <class R>
+Prim<R> cell_prim(const Field& F, const Params& P, Pt p) {
+  R chi = load<R>(F, CHI, p);
+  R gt[3][3], gtu[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) gt[i][j] = F.at(GT + sym(i, j), p);
-  inverse_sym3<double>(gt, gtu, nullptr);
-  double chi32 = chi * std::sqrt(chi);
+    for (int j = 0; j < 3; ++j) gt[i][j] = load<R>(F, GT + sym(i, j), p);
+  inverse_sym3<R>(gt, gtu, nullptr);
+  R chi32 = chi * sqrt(chi);
   int q = P.ifl();
-  double E = F.at(q, p) * chi32, J[3];
-  for (int i = 0; i < 3; ++i) J[i] = F.at(q + 1 + i, p) * chi32;
-  double J2 = 0.0;
+  R E = load<R>(F, q, p) * chi32, J[3];
+  for (int i = 0; i < 3; ++i) J[i] = load<R>(F, q + 1 + i, p) * chi32;
+  R J2 = R(0.0);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) J2 = J2 + chi * gtu[i][j] * J[i] * J[j];
-  Prim r;
-  r.rho = fluid_rho<double>(E, J2, P.w);
-  double EP = E + P.w * r.rho;
+  Prim<R> r;
+  r.rho = fluid_rho<R>(E, J2, P.w);
+  R EP = E + R(P.w) * r.rho;
   for (int i = 0; i < 3; ++i) r.v[i] = J[i] / EP;
   return r;
 }
 
 template <class R>
 void kt_face_flux(const Field& F, const Params& P, Pt p, int d, R H[4]) {
-  Prim c[4];
-  for (int o = -1; o <= 2; ++o) c[o + 1] = cell_prim(F, P, shift(p, d, o));
+  using PT = typename std::conditional<is_ad<R>::value, R, double>::type;
+  Prim<PT> c[4];
+  for (int o = -1; o <= 2; ++o) c[o + 1] = cell_prim<PT>(F, P, shift(p, d, o));
   // reconstructed left (from cell p) and right (from cell p+1) face states
   R qL[4], qR[4];
   for (int m = 0; m < 4; ++m) {
@@ -776,13 +828,13 @@ void kt_face_flux(const Field& F, const Params& P, Pt p, int d, R H[4]) {
   }
   // face geometry
   Pt p1 = shift(p, d, 1);
-  R chi = R(0.5) * (R(F.at(CHI, p)) + R(F.at(CHI, p1)));
-  R alpha = R(0.5) * (R(F.at(ALP, p)) + R(F.at(ALP, p1)));
-  R betad = R(0.5) * (R(F.at(BET + d, p)) + R(F.at(BET + d, p1)));
+  R chi = R(0.5) * (load<R>(F, CHI, p) + load<R>(F, CHI, p1));
+  R alpha = R(0.5) * (load<R>(F, ALP, p) + load<R>(F, ALP, p1));
+  R betad = R(0.5) * (load<R>(F, BET + d, p) + load<R>(F, BET + d, p1));
   R gt[3][3], gtu[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = i; j < 3; ++j)
-      gt[i][j] = gt[j][i] = R(0.5) * (R(F.at(GT + sym(i, j), p)) + R(F.at(GT + sym(i, j), p1)));
+      gt[i][j] = gt[j][i] = R(0.5) * (load<R>(F, GT + sym(i, j), p) + load<R>(F, GT + sym(i, j), p1));
   inverse_sym3<R>(gt, gtu, nullptr);
   R gu[3][3];
   for (int i = 0; i < 3; ++i)
@@ -843,9 +895,13 @@ void point_rhs(const Field& F, const Params& P, Pt p, double t, R* out) {
     for (int d = 0; d < 3; ++d) {
       R Hp[4], Hm[4];
       kt_face_flux<R>(F, P, p, d, Hp);
-      double hm[4];
-      kt_face_flux<double>(F, P, shift(p, d, -1), d, hm);  // the neighbour's own face
-      for (int m = 0; m < 4; ++m) Hm[m] = R(hm[m]);
+      if constexpr (is_ad<R>::value) {
+        kt_face_flux<R>(F, P, shift(p, d, -1), d, Hm);
+      } else {
+        double hm[4];
+        kt_face_flux<double>(F, P, shift(p, d, -1), d, hm);  // the neighbour's own face
+        for (int m = 0; m < 4; ++m) Hm[m] = R(hm[m]);
+      }
       for (int m = 0; m < 4; ++m) out[q + m] = out[q + m] - (Hp[m] - Hm[m]) / R(F.g->h[d]);
     }
   }
@@ -1113,6 +1169,45 @@ void oracle_init(const int* n, const double* h, const double* x0, const double* 
                  double* state) {
   Grid g = make_grid(n, h, x0);
   init_all(g, unpack_params(params), id, state);
+}
+
+/* Reverse mode of the right-hand side: out = (dF/dU)^T w, w and out in state
+ * layout, by recording F(U) on a tape (every point, every operation) and one
+ * reverse sweep.  Single-threaded; meant for tiny grids (tape ~1e4 nodes per
+ * point). */
+void oracle_rhs_vjp(const int* n, const double* h, const double* x0, const double* params, const double* state,
+                    double t, const double* w, double* out) {
+  Grid g = make_grid(n, h, x0);
+  Params P = unpack_params(params);
+  Field F{&g, state};
+  const int nf = P.nf();
+  const long N = g.npts(), M = (long)nf * N;
+  g_tape.clear();
+  g_tape.reserve((size_t)M + (size_t)N * 20000);
+  for (long m = 0; m < M; ++m) g_tape.push_back(TapeNode{-1, -1, 0.0, 0.0});  // leaves = state entries
+  std::vector<std::pair<long, double>> seeds;
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        AD o[NFMAX];
+        Pt p{{i, j, k}};
+        point_rhs<AD>(F, P, p, t, o);
+        long idx = (k * g.n[1] + j) * g.n[0] + i;
+        for (int f = 0; f < nf; ++f)
+          if (o[f].id >= 0) seeds.push_back({o[f].id, w[f * N + idx]});
+      }
+  std::vector<double> adj(g_tape.size(), 0.0);
+  for (auto& sd : seeds) adj[sd.first] += sd.second;
+  for (long q = (long)g_tape.size() - 1; q >= M; --q) {
+    const double a = adj[q];
+    if (a == 0.0) continue;
+    const TapeNode& nd = g_tape[q];
+    if (nd.a >= 0) adj[nd.a] += a * nd.da;
+    if (nd.b >= 0) adj[nd.b] += a * nd.db;
+  }
+  for (long m = 0; m < M; ++m) out[m] = adj[m];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
 }
 
 /* Algorithmic operation count of one RHS evaluation at one point:
