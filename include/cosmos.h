@@ -56,6 +56,11 @@ extern "C" {
 #define COSMOS_OP_RK4 1
 #define COSMOS_OP_CONSTRAINTS 2
 #define COSMOS_OP_INIT 3
+/* ... and for cosmos_adjoint_workspace_bytes */
+#define COSMOS_OP_VJP 4
+#define COSMOS_OP_ADJOINT 5
+#define COSMOS_OP_INIT_VJP 6
+#define COSMOS_OP_DIAG 7
 
 typedef struct {
   int nx, ny, nz; /* grid points per direction, each >= 1 */
@@ -150,6 +155,56 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
  * ws: COSMOS_OP_CONSTRAINTS bytes. */
 int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
                        double norms_host[8], void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Reverse mode (adjoint) of the evolution, for gradients of collapse
+ * diagnostics with respect to the initial curvature perturbation.  Covers the
+ * BSSN + fluid system (scalar off); every reverse step is the exact transpose
+ * of the corresponding discrete forward step (minmod, max and |.| take the
+ * derivative of the branch taken).
+ * ------------------------------------------------------------------------ */
+
+/* Workspace for COSMOS_OP_VJP, COSMOS_OP_ADJOINT, COSMOS_OP_INIT_VJP or
+ * COSMOS_OP_DIAG (0 if the arguments are invalid). */
+size_t cosmos_adjoint_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int op);
+
+/* v = (dF/dU)^T w: the transpose of the right-hand side's Jacobian at state
+ * U and time t applied to w (both in state layout).  v is overwritten. */
+int cosmos_rhs_vjp(const cosmos_grid* g, const cosmos_params* p, const double* U, const double* w, double* v,
+                   double t, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of one RK4 step U_{n+1} = Phi(U_n) from time t with step dt:
+ * lam_n = (dPhi/dU_n)^T lam_np1.  Recomputes the stage states from U_n.
+ * lam_n may equal lam_np1 (in place). */
+int cosmos_adjoint_step(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* lam_np1,
+                        double* lam_n, double t, double dt, void* ws, size_t ws_bytes, void* stream);
+
+/* FLRW initial data (as cosmos_init_grid kind 1) from a per-point curvature
+ * perturbation zeta (one double per point, state row layout):
+ * chi = exp(-2 zeta)/a0^2, gt = delta, K = -3 H0, alpha = 1, fluid at rest
+ * with E from the discrete Hamiltonian constraint.  ws: COSMOS_OP_INIT bytes. */
+int cosmos_init_zeta(const cosmos_grid* g, const cosmos_params* p, const double* zeta, double a0, double* state,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* zeta_bar = (d state0 / d zeta)^T lam0 for the map of cosmos_init_zeta
+ * (state0 = its output).  ws: COSMOS_OP_INIT_VJP bytes. */
+int cosmos_init_zeta_vjp(const cosmos_grid* g, const cosmos_params* p, const double* state0, const double* lam0,
+                         double* zeta_bar, void* ws, size_t ws_bytes, void* stream);
+
+/* Compaction function about the centre grid point (nx/2, ny/2, nz/2), fluid on:
+ *   C(r_k) = 2 dM(r_k) / R(r_k),  r_k = k h,  k = 1..kmax (kmax < min(n)/2),
+ *   dM = h^3 sum_{|x - c| < r_k} (tau~ - Ebar sqrt(gamma)),  Ebar = sum tau~ / sum sqrt(gamma),
+ *   R = r_k * mean of chi^{-1/2} over the 6 axis points at distance r_k.
+ * Writes C_host[k-1] and aux_host[4 kmax + 2] (per k: S, V, R, dM; then the
+ * box sums of tau~ and sqrt(gamma)) for cosmos_compaction_vjp.  Sums run in a
+ * fixed order (deterministic).  Synchronous.  ws: COSMOS_OP_DIAG bytes. */
+int cosmos_compaction(const cosmos_grid* g, const cosmos_params* p, const double* state, double* C_host, int kmax,
+                      double* aux_host, void* ws, size_t ws_bytes, void* stream);
+
+/* lam = cbar * d C(r_kstar) / d state (state layout, overwritten), with the
+ * aux_host written by cosmos_compaction for the same state. */
+int cosmos_compaction_vjp(const cosmos_grid* g, const cosmos_params* p, const double* state, int kstar, int kmax,
+                          const double* aux_host, double cbar, double* lam, void* stream);
 
 /* ------------------------------------------------------------------------
  * Batched evolution of many independent grids (a threshold scan: one

@@ -10,7 +10,9 @@ import sys
 
 from . import bssn
 from . import fluid as fluid_dsl
-from .expr import emit_function, op_counts
+from .expr import Ex, emit_function, op_counts, vjp
+
+ADJOINT_VARIANTS = ("vac", "fluid")
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")
@@ -52,6 +54,22 @@ def render() -> dict:
         body.append(_table_fn("d2_field", L["d2"]))
         body.append(emit_function(g, "rhs", L["names"], out, ["AlgebraParams"]))
         body.append(emit_function(g, "constraints", L["names"], g.constraints, ["AlgebraParams"]))
+        if name in ADJOINT_VARIANTS:
+            # reverse mode: in[0 .. NIN) as for rhs, in[NIN + f] = cotangent of out[f];
+            # out[k] = sum_f cot_f d out_f / d in[k]
+            w = [g.input(f"w{f}") for f in range(L["nf"])]
+            wrt = [Ex(g, g.inputs[nm]) for nm in L["names"]]
+            adj = vjp(g, out, w, wrt)
+            stats.append((name + "_vjp", op_counts(g, adj)))
+            body.append(f"// reverse mode of rhs: ops {dict(sorted(op_counts(g, adj).items()))}")
+            body.append(emit_function(g, "rhs_vjp", L["names"] + [f"w{f}" for f in range(L["nf"])], adj,
+                                      ["AlgebraParams"]))
+        if name == "vac":
+            # reverse mode of H (first constraint) w.r.t. chi, d chi, dd chi: initial-data adjoint
+            hb = g.input("hb")
+            chi_in = ["u0"] + [f"d0_{k}" for k in range(3)] + [f"dd0_{m}" for m in range(6)]
+            adjh = vjp(g, g.constraints[:1], [hb], [Ex(g, g.inputs[nm]) for nm in chi_in])
+            body.append(emit_function(g, "ham_vjp_chi", L["names"] + ["hb"], adjh, ["AlgebraParams"]))
         body.append(f"}}  // namespace alg_{name}\n")
     files["bssn_algebra.cuh"] = "\n".join(body)
     fb = [FLUID_HEADER]
@@ -59,12 +77,20 @@ def render() -> dict:
     stats.append(("prim", op_counts(g, out)))
     fb.append("// inputs: " + ", ".join(names))
     fb.append(emit_function(g, "fluid_prim", names, out, ["FluidParams"]))
+    qb = [g.input(f"qb{m}") for m in range(4)]
+    adj = vjp(g, out, qb, [Ex(g, g.inputs[nm]) for nm in names])
+    fb.append("// reverse mode: in[11 + m] = cotangent of (rho, v0, v1, v2)[m]; out = cotangents of the inputs")
+    fb.append(emit_function(g, "fluid_prim_vjp", names + [f"qb{m}" for m in range(4)], adj, ["FluidParams"]))
     for d in range(3):
         g, names, out = fluid_dsl.face_flux(d)
         stats.append((f"face{d}", op_counts(g, out)))
         if d == 0:
             fb.append("// face-flux inputs: " + ", ".join(names))
         fb.append(emit_function(g, f"fluid_face_flux_{d}", names, out, ["FluidParams"]))
+        hb = [g.input(f"hb{m}") for m in range(4)]
+        adj = vjp(g, out, hb, [Ex(g, g.inputs[nm]) for nm in names])
+        fb.append(emit_function(g, f"fluid_face_flux_{d}_vjp", names + [f"hb{m}" for m in range(4)], adj,
+                                ["FluidParams"]))
     files["fluid_algebra.cuh"] = "\n".join(fb)
     return files, stats
 

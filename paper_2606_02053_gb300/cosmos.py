@@ -23,6 +23,7 @@ COSMOS_EWORKSPACE = -3
 COSMOS_EALIGN = -4
 COSMOS_ENONFINITE = -5
 COSMOS_OP_RHS, COSMOS_OP_RK4, COSMOS_OP_CONSTRAINTS, COSMOS_OP_INIT = 0, 1, 2, 3
+COSMOS_OP_VJP, COSMOS_OP_ADJOINT, COSMOS_OP_INIT_VJP, COSMOS_OP_DIAG = 4, 5, 6, 7
 
 
 class cosmos_grid(ctypes.Structure):
@@ -71,6 +72,15 @@ _SIGS = {
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_probe_fp64": ([_P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_adjoint_workspace_bytes": ([_G, _PP, ctypes.c_int], ctypes.c_size_t),
+    "cosmos_rhs_vjp": ([_G, _PP, _P, _P, _P, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_adjoint_step": ([_G, _PP, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_init_zeta": ([_G, _PP, _P, _D, _P, _P, _S, _P], ctypes.c_int),
+    "cosmos_init_zeta_vjp": ([_G, _PP, _P, _P, _P, _P, _S, _P], ctypes.c_int),
+    "cosmos_compaction": ([_G, _PP, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                           ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
+    "cosmos_compaction_vjp": ([_G, _PP, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _D, _P, _P],
+                              ctypes.c_int),
     "cosmos_batch_workspace_bytes": ([ctypes.c_int, _G, _PP, ctypes.c_int], ctypes.c_size_t),
     "cosmos_batch_plan": ([ctypes.c_int, _G, _PP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(cosmos_batch_tuning), _P, _S,
@@ -185,6 +195,49 @@ def cosmos_probe_fp64(scratch, stream=None) -> float:
     out = ctypes.c_double(0.0)
     check(lib().cosmos_probe_fp64(_ptr(scratch), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+def cosmos_adjoint_workspace_bytes(g, p, op) -> int:
+    return lib().cosmos_adjoint_workspace_bytes(ctypes.byref(g), ctypes.byref(p), int(op))
+
+
+def cosmos_rhs_vjp(g, p, U, w, v, t, ws=None, stream=None) -> int:
+    wp, nb = _ws(ws)
+    return lib().cosmos_rhs_vjp(ctypes.byref(g), ctypes.byref(p), _ptr(U), _ptr(w), _ptr(v), float(t), wp, nb,
+                                _stream(stream))
+
+
+def cosmos_adjoint_step(g, p, U_n, lam_np1, lam_n, t, dt, ws=None, stream=None) -> int:
+    wp, nb = _ws(ws)
+    return lib().cosmos_adjoint_step(ctypes.byref(g), ctypes.byref(p), _ptr(U_n), _ptr(lam_np1), _ptr(lam_n),
+                                     float(t), float(dt), wp, nb, _stream(stream))
+
+
+def cosmos_init_zeta(g, p, zeta, a0, state, ws=None, stream=None) -> int:
+    wp, nb = _ws(ws)
+    return lib().cosmos_init_zeta(ctypes.byref(g), ctypes.byref(p), _ptr(zeta), float(a0), _ptr(state), wp, nb,
+                                  _stream(stream))
+
+
+def cosmos_init_zeta_vjp(g, p, state0, lam0, zeta_bar, ws=None, stream=None) -> int:
+    wp, nb = _ws(ws)
+    return lib().cosmos_init_zeta_vjp(ctypes.byref(g), ctypes.byref(p), _ptr(state0), _ptr(lam0), _ptr(zeta_bar),
+                                      wp, nb, _stream(stream))
+
+
+def cosmos_compaction(g, p, state, kmax, ws=None, stream=None):
+    """Returns (code, C[kmax] list, aux ctypes array)."""
+    C = (ctypes.c_double * kmax)()
+    aux = (ctypes.c_double * (4 * kmax + 2))()
+    wp, nb = _ws(ws)
+    code = lib().cosmos_compaction(ctypes.byref(g), ctypes.byref(p), _ptr(state), C, int(kmax), aux, wp, nb,
+                                   _stream(stream))
+    return code, list(C), aux
+
+
+def cosmos_compaction_vjp(g, p, state, kstar, kmax, aux, cbar, lam, stream=None) -> int:
+    return lib().cosmos_compaction_vjp(ctypes.byref(g), ctypes.byref(p), _ptr(state), int(kstar), int(kmax), aux,
+                                       float(cbar), _ptr(lam), _stream(stream))
 
 
 def cosmos_batch_workspace_bytes(grids, p, max_steps) -> int:

@@ -123,6 +123,13 @@ cudaError_t launch_constraints_fluid(const ConstraintArgs& a, cudaStream_t s);
 cudaError_t launch_constraints_scalar(const ConstraintArgs& a, cudaStream_t s);
 cudaError_t launch_constraints_fluid_scalar(const ConstraintArgs& a, cudaStream_t s);
 
+// adjoint_<variant>.cu
+struct VjpArgs;
+cudaError_t launch_vjp_vac(const VjpArgs& a, cudaStream_t s);
+cudaError_t launch_vjp_fluid(const VjpArgs& a, cudaStream_t s);
+cudaError_t launch_init_zeta_vjp(const DevGrid& g, const Coef& c, const AlgebraParams& ap, const double* U,
+                                 const double* lam, double* CB10, int fluid, double* zbar, cudaStream_t s);
+
 // fluid.cu
 cudaError_t launch_fluid_prim(const DevGrid& g, const double* U, double* prim, double w, cudaStream_t s);
 cudaError_t launch_fluid_flux(const DevGrid& g, const double* U, const double* prim, double* flux, double w,
