@@ -37,11 +37,14 @@ STATE_FIELDS = 24
 BYTES_PER_POINT_STAGE = [8 * 3 * 24, 8 * 5 * 24, 8 * 5 * 24, 8 * 4 * 24]
 # RK4 combine flops per field per stage (stage 1: 2; 2-3: 4; 4: 3)
 COMBINE_FLOPS = [2, 4, 4, 3]
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one stage-1 launch
-# of the vacuum stage kernel, from the committed ncu capture of the 96^3 case
-# (3.027 + 7.288 GB), and the hash of the kernel sources it was taken on.  Reported scaled to the bench
-# grid by points; null when the kernel sources differ from the profiled ones.
-NCU_TRAFFIC = {"sources_sha256_16": "c1e137dd9707b898", "grid": 96, "bytes_per_launch": 10.314704e9}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each pass of the vacuum stage, from the committed ncu capture of the 96^3
+# case, and the hash of the kernel sources it was taken on.  Reported scaled to
+# the bench grid by points; null when the kernel sources differ from the
+# profiled ones.
+NCU_TRAFFIC = {"sources_sha256_16": "none", "grid": 96, "bytes_per_launch": {"derivative": None, "algebra": None}}
+# derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
+DERIV_DOUBLES = 162
 KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_vac.cu", "generated/bssn_algebra.cuh"]
 
 
@@ -63,7 +66,81 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "scan", "adjoint"],
+                    help="sweep: single 256^3 grid (headline); scan: 64-instance batched threshold scan; "
+                         "adjoint: gradients of collapse diagnostics at 96^3")
+    ap.add_argument("--adjoint-steps", type=int, default=256, help=argparse.SUPPRESS)
+    ap.add_argument("--adjoint-grid", type=int, default=96, help=argparse.SUPPRESS)
+    ap.add_argument("--instances", type=int, default=64, help=argparse.SUPPRESS)
     return ap.parse_args()
+
+
+def scan_workload(args):
+    """Batched threshold scan: 64 FLRW + zeta instances on uneven 64^3..96^3 grids
+    (radiation fluid w = 1/3, H0 L = 40, mu, sigma, axis ratios from SplitMix64
+    seed 2606), dt = h/4 per instance.  Times the batched CUDA-graph run against
+    the plain per-instance loop (cosmos_rk4_step per grid) on the same GPU, over
+    the same steps, and checks that both give the same states."""
+    import torch
+
+    from paper_2606_02053_gb300 import build, inputs
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.batch import BatchScan
+
+    build.build()
+    inst = inputs.scan_instances(args.instances, seed=2606)
+    p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
+    grids, dts, ids = [], [], []
+    for d in inst:
+        n = d["n"]
+        h = 1.0 / n
+        grids.append(C.make_grid(n, h, x0=(-(n // 2) * h,) * 3))
+        dts.append(0.25 * h)
+        ids.append(C.make_id(1, mu=d["mu"], sigma=d["sigma"], q=d["q"]))
+    total_pts = float(sum(g.nx * g.ny * g.nz for g in grids))
+    K, W = args.steps, args.warmup
+    b = BatchScan(grids, p, dts, max_steps=W + K)
+    b.init(ids)
+    init_states = [s.clone() for s in b.states]
+    tune = b.autotune(reps=2)
+    stream = torch.cuda.Stream()
+    b.run(0, W, use_graph=True, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.run(W, K, use_graph=True, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    # plain per-instance loop, same steps, one shared workspace
+    nbmax = max(C.cosmos_workspace_bytes(g, p, C.COSMOS_OP_RK4) for g in grids)
+    ws = torch.empty((nbmax + 7) // 8, dtype=torch.float64, device="cuda")
+    loop_states = [s.clone() for s in init_states]
+    for g, st, dt in zip(grids, loop_states, dts):
+        for k in range(W):
+            C.check(C.cosmos_rk4_step(g, p, st, k * dt, dt, ws))
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for g, st, dt in zip(grids, loop_states, dts):
+        for k in range(W, W + K):
+            C.check(C.cosmos_rk4_step(g, p, st, k * dt, dt, ws))
+    f1.record()
+    torch.cuda.synchronize()
+    t_loop = f0.elapsed_time(f1) * 1e-3
+    max_diff = max(float((a - c).abs().max()) for a, c in zip(b.states, loop_states))
+    value = total_pts * K / t_batch
+    line = {"metric": "batched threshold-scan FP64 grid-point RK4 updates/sec (64 instances, 64^3-96^3)",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "flrw_zeta_scan_64_instances_fluid_w1/3", "instances": len(grids),
+                       "points_total": int(total_pts), "grid_sizes": [g.nx for g in grids]},
+            "per_instance_loop_value": total_pts * K / t_loop, "batched_speedup": t_loop / t_batch,
+            "batched_vs_loop_max_abs_diff": max_diff, "autotune": tune,
+            "gpu_launches": K * 4 * 3}
+    print(json.dumps(line), flush=True)
 
 
 class ClockSampler:
@@ -153,16 +230,111 @@ def cpu_baseline_sample(n, planes, repeats=1, state=None):
     pts = planes * n * n
     per_step = 4.0 * dt
     counts = O.flop_count(og, op, state)
+    parts = O.flop_count_parts(og, op, state)
     return {"value": pts / per_step, "seconds_per_step": per_step, "cores": O.max_threads(),
             "sample": f"oracle RHS on {planes} of {n} z-planes ({pts} points) x4 stages per RK4 step, "
                       f"{repeats} repeat(s); host threads {O.max_threads()}",
-            "flops": counts}
+            "flops": counts, "flops_parts": parts}
+
+
+def adjoint_workload(args):
+    """96^3 FLRW + Gaussian zeta (mu = 0.6, sigma = L/8, radiation fluid, H0 L = 40),
+    256 RK4 steps (dt = h/4), checkpoints every 16 steps.  Gradients of the minimum
+    central lapse and of the peak compaction with respect to mu and to zeta at every
+    point, by the adjoint; checked with central differences (h = 1e-6) on mu, on 8
+    random points and on 2 random directions of zeta.  The adjoint's cost is set
+    against the finite-difference loop (2 forward runs per scalar)."""
+    import numpy as np
+    import torch
+
+    from paper_2606_02053_gb300 import build
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.adjoint import CollapseRun, CosmosAdjoint
+
+    build.build()
+    n, steps = args.adjoint_grid, args.adjoint_steps
+    h = 1.0 / n
+    p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
+    run = CollapseRun(n, p, dt=0.25 * h, steps=steps, checkpoint_every=16)
+    x = (-(n // 2) + torch.arange(n, dtype=torch.float64, device="cuda")) * h
+    Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+    shape = torch.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * (1.0 / 8.0) ** 2)).reshape(-1).contiguous()
+    mu0 = 0.6
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    run.forward(mu0 * shape)  # warm-up
+    mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
+    zeta = (mu * shape).contiguous()
+    zeta.retain_grad()
+    out, t_fwd = timed(lambda: CosmosAdjoint.apply(zeta, run))
+    (g_mu_min,), t_b1 = timed(lambda: torch.autograd.grad(out[0], mu, retain_graph=True))
+    # per-point gradients of each diagnostic (one reverse run each)
+    amin, cpeak, rec = run.forward((mu0 * shape).contiguous())
+    zb_min, t_bmin = timed(lambda: run.backward(rec, 1.0, 0.0))
+    zb_comp, t_bcomp = timed(lambda: run.backward(rec, 0.0, 1.0))
+    g_mu_comp = float(torch.dot(zb_comp, shape))
+    g_mu_min_v = float(g_mu_min)
+    hfd = 1e-6
+    checks = []
+
+    def fd(direction, label):
+        zp = (mu0 * shape + hfd * direction).contiguous()
+        zm = (mu0 * shape - hfd * direction).contiguous()
+        a1, c1, _ = run.forward(zp)
+        a2, c2, _ = run.forward(zm)
+        fmin, fcomp = (a1 - a2) / (2 * hfd), (c1 - c2) / (2 * hfd)
+        amn = float(torch.dot(zb_min, direction))
+        acp = float(torch.dot(zb_comp, direction))
+        checks.append({"what": label, "fd_min_lapse": fmin, "adj_min_lapse": amn, "fd_compaction": fcomp,
+                       "adj_compaction": acp})
+
+    fd(shape, "mu")
+    rng = np.random.default_rng(2606)
+    centre = n // 2
+    for _ in range(8):
+        i, j, k = (int(v) for v in rng.integers(centre - n // 8, centre + n // 8, size=3))
+        e = torch.zeros_like(shape)
+        e[(k * n + j) * n + i] = 1.0
+        fd(e, f"zeta[{i},{j},{k}]")
+    for r in range(2):
+        d = torch.from_numpy(rng.standard_normal(n ** 3)).cuda() * shape
+        fd(d, f"random direction {r}")
+
+    def rel(a, b):
+        return abs(a - b) / max(abs(a), abs(b), 1e-300)
+
+    worst_min = max(rel(c["fd_min_lapse"], c["adj_min_lapse"]) for c in checks)
+    worst_comp = max(rel(c["fd_compaction"], c["adj_compaction"]) for c in checks)
+    t_adj = t_fwd + t_bmin + t_bcomp
+    nscal = n ** 3
+    line = {"metric": "adjoint gradient of collapse diagnostics (96^3, 256 steps): speedup over finite differences",
+            "value": (2 * nscal * t_fwd) / t_adj, "unit": "x (FD loop time / adjoint time, all zeta points)",
+            "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "flrw_zeta_adjoint", "grid": n, "mu": mu0, "sigma": 0.125, "H0L": 40.0,
+                       "checkpoint_every": 16},
+            "forward_s": t_fwd, "backward_min_lapse_s": t_bmin, "backward_compaction_s": t_bcomp,
+            "min_central_lapse": float(out[0]), "min_lapse_step": rec["nstar"], "peak_compaction": float(out[1]),
+            "peak_shell": rec["kstar"], "dmin_dmu": g_mu_min_v, "dcomp_dmu": g_mu_comp,
+            "speedup_11_scalars": (2 * 11 * t_fwd) / t_adj, "fd_checks": checks,
+            "worst_rel_diff_min_lapse": worst_min, "worst_rel_diff_compaction": worst_comp}
+    print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "scan":
+        return scan_workload(args)
+    if args.workload == "adjoint":
+        return adjoint_workload(args)
 
     import numpy as np
     import torch
@@ -195,19 +367,22 @@ def main():
     stream = torch.cuda.current_stream()
 
     def stage_calls(t, events=None):
+        """One RK4 step as 4 stages x (derivative pass, algebra pass); events
+        bracket each pass on the launching stream."""
         seq = [(ev.state, U1), (U1, U2), (U2, U1), (U1, None)]
         for s, (src, dst) in enumerate(seq, start=1):
-            if events is not None:
-                events[s - 1][0].record(stream)
-            C.check(C.cosmos_rk4_stage(g, p, s, src, ev.state, dst, acc, t, dt, ev.ws_rhs, stream))
-            if events is not None:
-                events[s - 1][1].record(stream)
+            for pss in (1, 2):
+                if events is not None:
+                    events[s - 1][pss - 1][0].record(stream)
+                C.check(C.cosmos_stage_pass(g, p, pss, s, src, ev.state, dst, acc, t, dt, ev.ws_rhs, stream))
+                if events is not None:
+                    events[s - 1][pss - 1][1].record(stream)
 
     for w in range(args.warmup):
         stage_calls(w * dt)
     torch.cuda.synchronize()
-    ev_pairs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(4)]
-                for _ in range(args.steps)]
+    ev_pairs = [[[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+                 for _ in range(4)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)
@@ -225,7 +400,9 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     elapsed = start.elapsed_time(stop) * 1e-3
-    stage_ms = [[ev_pairs[k][s][0].elapsed_time(ev_pairs[k][s][1]) for k in range(args.steps)] for s in range(4)]
+    # pass_ms[pass][stage] = list over steps
+    pass_ms = [[[ev_pairs[k][s][q][0].elapsed_time(ev_pairs[k][s][q][1]) for k in range(args.steps)] for s in range(4)]
+               for q in range(2)]
     if dist:
         tt = torch.tensor([elapsed], device=f"cuda:{local}")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -233,7 +410,7 @@ def main():
     nranks = ws_
     pts = float(n) ** 3
     value = nranks * pts * args.steps / elapsed
-    gpu_launches = 4 * args.steps
+    gpu_launches = 8 * args.steps  # per stage: derivative kernel + algebra kernel
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     nbytes = ev.state.numel() * 8
@@ -268,31 +445,46 @@ def main():
     if not args.no_cpu_baseline:
         host_state = ev.get()
         cpu = cpu_baseline_sample(n, planes=16, repeats=1, state=host_state)
-    avg_stage = [statistics.mean(v) * 1e-3 for v in stage_ms]
-    dom = max(range(4), key=lambda s: avg_stage[s])
-    roof = None
+    # average launch duration per kernel (over the 4 stages and all steps)
+    avg = {name: statistics.mean([x for st in pass_ms[q] for x in st]) * 1e-3
+           for q, name in enumerate(["derivative", "algebra"])}
+    stage_avg = [statistics.mean(pass_ms[0][s]) + statistics.mean(pass_ms[1][s]) for s in range(4)]
+    roof, roof2 = None, None
     if cpu is not None:
-        c = cpu["flops"]
-        rhs_flops = c["add"] + c["mul"] + c["div"] + c["sqrt"]
-        flops_launch = pts * (rhs_flops + COMBINE_FLOPS[dom] * STATE_FIELDS)
-        achieved = flops_launch / avg_stage[dom] / 1e12
+        parts = cpu["flops_parts"]
+        fl = lambda d: d["add"] + d["mul"] + d["div"] + d["sqrt"]  # noqa: E731
+        per_point = {"derivative": fl(parts["derivatives"]) + fl(parts["ko"]),
+                     "algebra": fl(parts["algebra"]) + statistics.mean(COMBINE_FLOPS) * STATE_FIELDS}
+        bytes_point = {"derivative": 8 * (STATE_FIELDS + DERIV_DOUBLES),
+                       "algebra": 8 * (DERIV_DOUBLES + statistics.mean([b / 8 for b in BYTES_PER_POINT_STAGE]))}
         peak = fp64_peak / 1e12
-        traffic = None
-        if kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"]:
-            traffic = NCU_TRAFFIC["bytes_per_launch"] * (n / NCU_TRAFFIC["grid"]) ** 3
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_note": "bytes per launch, ncu at 96^3 scaled by points",
-                "kernel": f"stage_kernel<T_vac, stage {dom + 1}>",
-                "peak_source": "FP64 DFMA throughput measured in this run (cosmos_probe_fp64); nominal 1.25",
-                "algorithmic_flops_per_point_rhs": rhs_flops,
-                "hbm_GBps_algorithmic": pts * BYTES_PER_POINT_STAGE[dom] / avg_stage[dom] / 1e9}
+        traffic_ok = kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"]
+
+        def roofline(name):
+            achieved = pts * per_point[name] / avg[name] / 1e12
+            tr = None
+            if traffic_ok:
+                tr = NCU_TRAFFIC["bytes_per_launch"][name] * (n / NCU_TRAFFIC["grid"]) ** 3
+            return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": tr,
+                    "traffic_note": "bytes per launch, ncu small-case capture scaled by points",
+                    "kernel": f"{name} pass ({'deriv_kernel' if name == 'derivative' else 'stage_kernel'}<T_vac>)",
+                    "avg_launch_ms": 1e3 * avg[name],
+                    "algorithmic_flops_per_point": per_point[name],
+                    "algorithmic_bytes_per_point": bytes_point[name],
+                    "hbm_GBps_algorithmic": pts * bytes_point[name] / avg[name] / 1e9,
+                    "peak_source": "FP64 DFMA throughput measured in this run (cosmos_probe_fp64); nominal 1.25"}
+
+        dom = max(avg, key=avg.get)
+        other = "algebra" if dom == "derivative" else "derivative"
+        roof, roof2 = roofline(dom), roofline(other)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": n, "fields": STATE_FIELDS, "dt_over_h": 0.25,
                        "parallelism": f"replicas{nranks}" if nranks > 1 else "single",
                        "l2": "inputs larger than L2 (3.2 GB state per level)"},
-            "stage_ms": [1e3 * s for s in avg_stage], "roofline": roof, "gpu_launches": gpu_launches,
+            "stage_ms": stage_avg, "roofline": roof, "roofline_other_kernel": roof2, "gpu_launches": gpu_launches,
             "e2e": e2e, "clocks": clk,
             "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"],
                                                       "kind": "oracle", "sample": cpu["sample"]}}

@@ -134,6 +134,17 @@ int cosmos_rhs(const cosmos_grid* g, const cosmos_params* p, const double* state
 int cosmos_rk4_stage(const cosmos_grid* g, const cosmos_params* p, int stage, const double* U_s, double* U_n,
                      double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
+/* One pass of a fused RK4 stage (arguments as cosmos_rk4_stage), so that
+ * the passes can be scheduled or timed separately:
+ *   pass 0: fluid primitives and face fluxes of U_s (nothing without fluid)
+ *   pass 1: derivative pass: finite differences and Kreiss-Oliger terms of U_s
+ *   pass 2: algebra pass + stage combine (needs passes 0 and 1 of this stage)
+ * Passes 0, 1, 2 in order equal one cosmos_rk4_stage call.  The workspace
+ * carries the intermediate results between passes. */
+int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, int stage, const double* U_s,
+                      double* U_n, double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes,
+                      void* stream);
+
 /* One classic RK4 step of size dt from time t, in place on `state`
  * (four cosmos_rk4_stage launches).  ws: COSMOS_OP_RK4 bytes
  * (two stage buffers, the accumulator and the fluid buffers). */

@@ -71,6 +71,7 @@ def lib():
         L.oracle_init.argtypes = [_I, _D, _D, _D, _D, _D]
         L.oracle_flop_count.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
         L.oracle_rhs_vjp.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D, _D]
+        L.oracle_flop_count_parts.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
         _lib = L
     return _lib
 
@@ -180,6 +181,17 @@ def init(g: OGrid, params, idarr):
     n, h, x0 = g.c()
     lib().oracle_init(n, h, x0, _dp(params), _dp(np.asarray(idarr, dtype=np.float64)), _dp(state))
     return state
+
+
+def flop_count_parts(g: OGrid, params, state, t=0.0):
+    """Counts {add, mul, div, sqrt, cmp} per part: derivatives, ko, algebra, flux."""
+    _check_state(g, params, state)
+    c = np.empty(20, dtype=np.float64)
+    n, h, x0 = g.c()
+    lib().oracle_flop_count_parts(n, h, x0, _dp(params), _dp(state), float(t), _dp(c))
+    names = ["add", "mul", "div", "sqrt", "cmp"]
+    return {part: dict(zip(names, c[5 * i:5 * i + 5].tolist()))
+            for i, part in enumerate(["derivatives", "ko", "algebra", "flux"])}
 
 
 def rhs_vjp(g: OGrid, params, state, w, t=0.0):

@@ -1229,4 +1229,47 @@ void oracle_flop_count(const int* n, const double* h, const double* x0, const do
   counts[4] = g_tally.cmp;
 }
 
+/* The same count split by part of the right-hand side: parts[4][5] =
+ * {derivatives (first, second, mixed), Kreiss-Oliger, pointwise algebra
+ * (incl. matter sources), fluid flux divergence} x {add, mul, div, sqrt, cmp}. */
+void oracle_flop_count_parts(const int* n, const double* h, const double* x0, const double* params,
+                             const double* state, double t, double* parts) {
+  Grid g = make_grid(n, h, x0);
+  Params P = unpack_params(params);
+  Field F{&g, state};
+  Pt p{{g.n[0] / 2, g.n[1] / 2, g.n[2] / 2}};
+  auto snap = [&](int part) {
+    parts[5 * part + 0] = g_tally.add;
+    parts[5 * part + 1] = g_tally.mul;
+    parts[5 * part + 2] = g_tally.div;
+    parts[5 * part + 3] = g_tally.sqrt;
+    parts[5 * part + 4] = g_tally.cmp;
+    g_tally = Tally{0, 0, 0, 0, 0};
+  };
+  g_tally = Tally{0, 0, 0, 0, 0};
+  Local<Cnt> L;
+  gather<Cnt>(F, P, p, L);
+  snap(0);
+  Cnt out[NFMAX];
+  const int nf = P.nf();
+  for (int f = 0; f < nf; ++f) {
+    if (P.fluid && f >= P.ifl() && f < P.ifl() + 4) continue;
+    out[f] = KO<Cnt>(F, f, p, P.sigma);
+  }
+  snap(1);
+  point_algebra<Cnt>(L, P, t, out);
+  // the KO terms are added to the algebra's outputs: one addition per field
+  for (int f = 0; f < nf; ++f)
+    if (!(P.fluid && f >= P.ifl() && f < P.ifl() + 4)) g_tally.add += 1;
+  snap(2);
+  if (P.fluid) {
+    for (int d = 0; d < 3; ++d) {
+      Cnt Hp[4];
+      kt_face_flux<Cnt>(F, P, p, d, Hp);
+      for (int m = 0; m < 4; ++m) out[m] = (Hp[m] - Cnt(0.0)) / Cnt(F.g->h[d]);  // difference + scaling
+    }
+  }
+  snap(3);
+}
+
 }  // extern "C"

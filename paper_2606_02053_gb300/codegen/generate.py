@@ -52,6 +52,8 @@ def render() -> dict:
         body.append(f"constexpr int NIN = {L['nin']};")
         body.append(_table_fn("d1_field", L["d1"]))
         body.append(_table_fn("d2_field", L["d2"]))
+        body.append(_slot_fn("d1_slot", L["d1"]))
+        body.append(_slot_fn("d2_slot", L["d2"]))
         body.append(emit_function(g, "rhs", L["names"], out, ["AlgebraParams"]))
         body.append(emit_function(g, "constraints", L["names"], g.constraints, ["AlgebraParams"]))
         if name in ADJOINT_VARIANTS:
@@ -100,6 +102,14 @@ def _table_fn(name, values):
     for m in reversed(range(len(values))):
         expr = f"(m == {m} ? {values[m]} : {expr})"
     return f"__host__ __device__ __forceinline__ constexpr int {name}(int m) {{ return {expr}; }}"
+
+
+def _slot_fn(name, values):
+    """Inverse table: field -> position in `values`, or -1."""
+    expr = "-1"
+    for m in reversed(range(len(values))):
+        expr = f"(f == {values[m]} ? {m} : {expr})"
+    return f"__host__ __device__ __forceinline__ constexpr int {name}(int f) {{ return {expr}; }}"
 
 
 FLUID_HEADER = """// GENERATED by paper_2606_02053_gb300/codegen/generate.py -- do not edit.

@@ -68,6 +68,7 @@ _SIGS = {
     "cosmos_rhs": ([_G, _PP, _P, _P, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_rk4_stage": ([_G, _PP, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_rk4_step": ([_G, _PP, _P, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_stage_pass": ([_G, _PP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
@@ -164,6 +165,12 @@ def cosmos_rk4_stage(g, p, stage, U_s, U_n, U_next, acc, t, dt, ws=None, stream=
     w, nb = _ws(ws)
     return lib().cosmos_rk4_stage(ctypes.byref(g), ctypes.byref(p), int(stage), _ptr(U_s), _ptr(U_n), _ptr(U_next),
                                   _ptr(acc), float(t), float(dt), w, nb, _stream(stream))
+
+
+def cosmos_stage_pass(g, p, pss, stage, U_s, U_n, U_next, acc, t, dt, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_stage_pass(ctypes.byref(g), ctypes.byref(p), int(pss), int(stage), _ptr(U_s), _ptr(U_n),
+                                   _ptr(U_next), _ptr(acc), float(t), float(dt), w, nb, _stream(stream))
 
 
 def cosmos_rk4_step(g, p, state, t, dt, ws=None, stream=None) -> int:

@@ -15,7 +15,7 @@ namespace cosmos {
 static size_t a256(size_t doubles) { return ((doubles * 8 + 255) & ~(size_t)255) / 8; }
 
 struct AdjLayout {
-  size_t U2, U3, U4, KB, KB2, LAM, CB, prim, flux, vprim, FC, VF, CB10, total_bytes;
+  size_t U2, U3, U4, KB, KB2, LAM, Dfw, CB, prim, flux, vprim, FC, VF, CB10, total_bytes;
 };
 
 static int nin_of(const cosmos_params* p) { return p->fluid ? alg_fluid::NIN : alg_vac::NIN; }
@@ -38,6 +38,7 @@ static AdjLayout adj_layout(const cosmos_grid* g, const cosmos_params* p, int op
     L.KB = take(nf * fs);
     L.KB2 = take(nf * fs);
     L.LAM = take(nf * fs);
+    L.Dfw = take((size_t)nder(0) * fs);
   }
   if (op == COSMOS_OP_ADJOINT || op == COSMOS_OP_VJP) {
     L.CB = take(nin_of(p) * fs);
@@ -132,6 +133,7 @@ static cudaError_t fwd_stage(const cosmos_grid* g, const cosmos_params* p, const
   a.acc = acc;
   a.cdt = cdt;
   a.bk = 2.0;
+  a.D = ws + L.Dfw;
   if (p->fluid) {
     cudaError_t e = launch_fluid_prim(a.g, U_s, ws + L.prim, p->w, s);
     if (e != cudaSuccess) return e;

@@ -92,7 +92,7 @@ int validate(const cosmos_grid* g, const cosmos_params* p) {
 
 // Workspace sub-buffers (each 256-byte aligned), in doubles from ws.
 struct WsLayout {
-  size_t prim, flux, stageA, stageB, acc, hm, partial, final_, total_bytes;
+  size_t prim, flux, D, stageA, stageB, acc, hm, partial, final_, total_bytes;
 };
 
 static WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
@@ -113,6 +113,7 @@ static WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) 
       L.prim = take(4 * fs);
       L.flux = take(12 * fs);
     }
+    L.D = take((size_t)nder(p->scalar) * fs);
     if (op == COSMOS_OP_RK4) {
       L.stageA = take(nf * fs);
       L.stageB = take(nf * fs);
@@ -256,10 +257,12 @@ static ConstraintLauncher constraint_launcher(const cosmos_params* p) {
   return launch_constraints_vac;
 }
 
-// Shared body of cosmos_rhs / cosmos_rk4_stage.
+// Shared body of cosmos_rhs / cosmos_rk4_stage / cosmos_stage_pass.
+// pass_mask bit 0: fluid pre-pass (primitives, face fluxes); bit 1: derivative
+// pass; bit 2: algebra pass + combine.
 static int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n,
                      double* out, double* acc, double t_stage, double cdt, double bk, double* ws,
-                     const WsLayout& L, cudaStream_t s) {
+                     const WsLayout& L, cudaStream_t s, int pass_mask = 7) {
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.g = make_devgrid(g);
@@ -272,15 +275,24 @@ static int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, con
   a.acc = acc;
   a.cdt = cdt;
   a.bk = bk;
+  a.D = ws + L.D;
   if (p->fluid) {
     double* prim = ws + L.prim;
     double* flux = ws + L.flux;
-    CK(launch_fluid_prim(a.g, U_s, prim, p->w, s));
-    CK(launch_fluid_flux(a.g, U_s, prim, flux, p->w, 24, s));
+    if (pass_mask & 1) {
+      CK(launch_fluid_prim(a.g, U_s, prim, p->w, s));
+      CK(launch_fluid_flux(a.g, U_s, prim, flux, p->w, 24, s));
+    }
     a.prim = prim;
     a.flux = flux;
   }
-  CK(stage_launcher(p)(a, mode, s));
+  if ((pass_mask & 6) == 6) {
+    CK(stage_launcher(p)(a, mode, s));
+  } else if (pass_mask & 2) {
+    CK(stage_launcher(p)(a, -1, s));  // derivative pass only
+  } else if (pass_mask & 4) {
+    CK(stage_launcher(p)(a, mode | 8, s));  // algebra pass only
+  }
   return COSMOS_OK;
 }
 
@@ -384,6 +396,24 @@ int cosmos_rk4_stage(const cosmos_grid* g, const cosmos_params* p, int stage, co
   const double cdt = stage == 1 || stage == 2 ? 0.5 * dt : (stage == 3 ? dt : dt / 6.0);
   return run_stage(g, p, modes[stage - 1], U_s, U_n, U_next, acc, t + c_stage[stage - 1] * dt, cdt, 2.0,
                    (double*)ws, L, (cudaStream_t)stream);
+}
+
+int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, int stage, const double* U_s,
+                      double* U_n, double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes,
+                      void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (pass < 0 || pass > 2 || stage < 1 || stage > 4 || !U_s || !U_n || !acc) return COSMOS_EINVAL;
+  if (stage < 4 && !U_next) return COSMOS_EINVAL;
+  if (U_s == acc || (stage < 4 && (U_s == U_next || U_next == acc || U_next == U_n))) return COSMOS_EINVAL;
+  if (stage == 4 && U_s == U_n) return COSMOS_EINVAL;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RHS);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
+  static const int modes[4] = {MODE_S1, MODE_S23, MODE_S23, MODE_S4};
+  const double cdt = stage == 1 || stage == 2 ? 0.5 * dt : (stage == 3 ? dt : dt / 6.0);
+  return run_stage(g, p, modes[stage - 1], U_s, U_n, U_next, acc, t + c_stage[stage - 1] * dt, cdt, 2.0,
+                   (double*)ws, L, (cudaStream_t)stream, 1 << pass);
 }
 
 int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,

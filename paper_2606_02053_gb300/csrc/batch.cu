@@ -40,10 +40,15 @@ static long max_tiles(const cosmos_grid& g) {
 }
 
 struct BatchLayout {
-  std::vector<size_t> A, B, acc, prim, flux;  // per instance, in doubles from ws
-  size_t args, tiles, kref;                   // byte offsets
+  std::vector<size_t> A, B, acc, prim, flux, D;  // per instance, in doubles from ws
+  size_t args, tiles, dtiles, kref;              // byte offsets
   size_t total;
 };
+
+// 32 x 4 tiles of every plane: the derivative pass's work list
+static long deriv_tiles(const cosmos_grid& g) {
+  return (long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+}
 
 static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_params* p, int max_steps) {
   BatchLayout L;
@@ -54,7 +59,7 @@ static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_pa
     off += al256(bytes);
     return o;
   };
-  long tiles = 0;
+  long tiles = 0, dtiles = 0;
   for (int i = 0; i < n; ++i) {
     const size_t fs = (size_t)grids[i].pitch * grids[i].ny * grids[i].nz;
     L.A.push_back(take(nf * fs * 8) / 8);
@@ -62,10 +67,13 @@ static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_pa
     L.acc.push_back(take(nf * fs * 8) / 8);
     L.prim.push_back(p->fluid ? take(4 * fs * 8) / 8 : 0);
     L.flux.push_back(p->fluid ? take(12 * fs * 8) / 8 : 0);
+    L.D.push_back(take((size_t)nder(p->scalar) * fs * 8) / 8);
     tiles += max_tiles(grids[i]);
+    dtiles += deriv_tiles(grids[i]);
   }
   L.args = take(sizeof(StageArgs) * 4 * (size_t)n);
   L.tiles = take(sizeof(BatchTile) * (size_t)tiles);
+  L.dtiles = take(sizeof(BatchTile) * (size_t)dtiles);
   L.kref = take(sizeof(double) * (size_t)max_steps * 4 * n);
   L.total = off;
   return L;
@@ -84,9 +92,10 @@ struct cosmos_batch_s {
   int sms = 0;
   char* ws = nullptr;
   BatchLayout L;
-  long ntiles = 0;
+  long ntiles = 0, ndtiles = 0;
   StageArgs* d_args = nullptr;  // [4][n]
   BatchTile* d_tiles = nullptr;
+  BatchTile* d_dtiles = nullptr;  // derivative-pass tiles (32 x 4)
   double* d_kref = nullptr;     // [max_steps][4][n]
   cudaGraphExec_t gexec = nullptr;
   int g_first = -1, g_steps = -1;
@@ -180,6 +189,7 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
   double* wsd = (double*)ws;
   b->d_args = (StageArgs*)(b->ws + L.args);
   b->d_tiles = (BatchTile*)(b->ws + L.tiles);
+  b->d_dtiles = (BatchTile*)(b->ws + L.dtiles);
   b->d_kref = (double*)(b->ws + L.kref);
 
   // per-stage, per-instance arguments (same fields as the single-grid stages)
@@ -205,6 +215,7 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
       a.acc = acc;
       a.cdt = cdt[s];
       a.bk = 2.0;
+      a.D = wsd + L.D[i];
       if (p->fluid) {
         a.prim = wsd + L.prim[i];
         a.flux = wsd + L.flux[i];
@@ -227,6 +238,23 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
     delete b;
     return COSMOS_ECUDA;
   }
+  {
+    std::vector<BatchTile> dt;
+    long most = 0;
+    for (int i = 0; i < n; ++i) most = std::max(most, deriv_tiles(grids[i]));
+    for (long w = 0; w < most; ++w)
+      for (int i = 0; i < n; ++i) {
+        const cosmos_grid& g = grids[i];
+        if (w >= deriv_tiles(g)) continue;
+        const int tx = (g.nx + BX - 1) / BX, ty = (g.ny + BY - 1) / BY;
+        dt.push_back(BatchTile{i, (int)(w % tx), (int)((w / tx) % ty), (int)(w / ((long)tx * ty))});
+      }
+    b->ndtiles = (long)dt.size();
+    if (cudaMemcpy(b->d_dtiles, dt.data(), sizeof(BatchTile) * dt.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      delete b;
+      return COSMOS_ECUDA;
+    }
+  }
   const int e = upload_tiles(b);
   if (e != COSMOS_OK) {
     delete b;
@@ -244,9 +272,7 @@ int cosmos_batch_set_tuning(cosmos_batch b, const cosmos_batch_tuning* tuning) {
 }
 
 static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStream_t s) {
-  typedef cudaError_t (*L)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                           cudaStream_t);
-  L launch = launch_batch_stage_vac;
+  BatchStageLauncher launch = launch_batch_stage_vac;
   if (b->p.fluid && b->p.scalar)
     launch = launch_batch_stage_fluid_scalar;
   else if (b->p.fluid)
@@ -262,7 +288,8 @@ static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStr
           launch_batch_fluid(args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
         return COSMOS_ECUDA;
       const double* kref = b->d_kref + ((size_t)st * 4 + stage) * b->n;
-      if (launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s) != cudaSuccess)
+      if (launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s, b->d_dtiles,
+                 b->ndtiles) != cudaSuccess)
         return COSMOS_ECUDA;
     }
   return COSMOS_OK;
@@ -299,10 +326,8 @@ int cosmos_batch_run(cosmos_batch b, int first_step, int steps, int use_graph, v
 int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stream) {
   if (!b || reps < 1 || !ms_out) return COSMOS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  typedef cudaError_t (*L)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                           cudaStream_t);
-  L launch = b->p.fluid ? (b->p.scalar ? launch_batch_stage_fluid_scalar : launch_batch_stage_fluid)
-                        : (b->p.scalar ? launch_batch_stage_scalar : launch_batch_stage_vac);
+  BatchStageLauncher launch = b->p.fluid ? (b->p.scalar ? launch_batch_stage_fluid_scalar : launch_batch_stage_fluid)
+                                         : (b->p.scalar ? launch_batch_stage_scalar : launch_batch_stage_vac);
   const dim3 grid(b->sms * b->tune.blocks_per_sm), block(b->tune.block_x, b->tune.block_y);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return COSMOS_ECUDA;
@@ -313,7 +338,8 @@ int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stre
         launch_batch_fluid(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
       rc = COSMOS_ECUDA;
     if (rc == COSMOS_OK &&
-        launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s) != cudaSuccess)
+        launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s, b->d_dtiles,
+               b->ndtiles) != cudaSuccess)
       rc = COSMOS_ECUDA;
   }
   cudaEventRecord(e1, s);

@@ -82,9 +82,14 @@ struct StageArgs {
   double* acc;                     // accumulator
   const double* __restrict__ prim; // fluid primitives [4][pts] (fluid only)
   const double* __restrict__ flux; // fluid face fluxes [3][4][pts] (fluid only)
+  double* D;                       // derivative-pass output [NDER][pts] (see stage_kernel.cuh)
   double cdt;                      // dt * c_{s+1}, or dt/6 in MODE_S4
   double bk;                       // accumulator weight (2 for stages 2, 3)
 };
+
+// Doubles per point of the derivative-pass buffer: first and second
+// derivatives plus the Kreiss-Oliger term of every non-fluid field.
+inline int nder(int scalar) { return 3 * (24 + 2 * scalar) + 6 * (11 + scalar) + 24 + 2 * scalar; }
 
 // One work item of a batch: instance `inst`; for 2D tiles (a, b, c) = (block
 // column, block row, z-plane), for linear runs a = first point index.
@@ -108,14 +113,18 @@ cudaError_t launch_stage_vac(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_scalar(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid_scalar(const StageArgs& a, int mode, cudaStream_t s);
+// batched stage: derivative pass over the 32 x 4 tile list (dtiles), algebra
+// pass over the tuned work list (tiles, mapping)
+typedef cudaError_t (*BatchStageLauncher)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
+                                          dim3, cudaStream_t, const BatchTile*, long);
 cudaError_t launch_batch_stage_vac(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                   cudaStream_t);
+                                   cudaStream_t, const BatchTile*, long);
 cudaError_t launch_batch_stage_fluid(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                     cudaStream_t);
+                                     cudaStream_t, const BatchTile*, long);
 cudaError_t launch_batch_stage_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                      cudaStream_t);
+                                      cudaStream_t, const BatchTile*, long);
 cudaError_t launch_batch_stage_fluid_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
-                                            dim3, cudaStream_t);
+                                            dim3, cudaStream_t, const BatchTile*, long);
 cudaError_t launch_batch_fluid(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping, double w,
                                dim3 grid, dim3 block, cudaStream_t s);
 cudaError_t launch_constraints_vac(const ConstraintArgs& a, cudaStream_t s);

@@ -11,6 +11,9 @@
 
 #include "common.cuh"
 
+#ifndef COSMOS_DERIV_MIN_BLOCKS
+#define COSMOS_DERIV_MIN_BLOCKS 5  // derivative pass: resident 128-thread blocks per SM
+#endif
 #ifndef COSMOS_STAGE_MIN_BLOCKS
 #define COSMOS_STAGE_MIN_BLOCKS 3  // resident 128-thread blocks per SM the register budget is sized for
 #endif
@@ -114,27 +117,163 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
   if constexpr (T::FLUID) in[T::NIN - 1] = ldg(prim, n.c);
 }
 
-// RHS + stage combine at one grid point (i, j, k) of one grid.
-template <class T, int MODE>
-__device__ __forceinline__ void stage_point(const StageArgs& a, const AlgebraParams& ap, int i, int j, int k) {
+// ---------------------------------------------------------------------------
+// Stage = derivative pass + algebra pass.
+//
+// Derivative pass (one 32 x 4 tile of one z-plane per block): writes every
+// finite difference the algebra needs, and the Kreiss-Oliger term of every
+// non-fluid field, into D (layout: D[3 m + d] first derivative d of the m-th
+// first-derivative field, D[3 ND1 + 6 m + p] second derivative p of the m-th
+// second-derivative field, D[NDER0 + ko_slot(f)] KO term of field f).  For the
+// second-derivative fields the first derivatives along y and z are computed
+// once per tile point (with a 2-point halo) into shared memory, and the mixed
+// derivatives are D_x(D_y f), D_x(D_z f), D_y(D_z f) of those values; along x
+// the neighbour differences d_k = f(+-k) - f0 are shared by D1, D2 and KO.
+// Algebra pass (any point mapping): the generated pointwise algebra on the
+// state values and D, KO and the fluid flux divergence, and the RK4 combine.
+// ---------------------------------------------------------------------------
+constexpr int TXH = BX + 4;  // tile width with the x halo
+
+template <class T>
+__device__ __forceinline__ int ko_slot(int f) {
+  return (T::FLUID && f >= 28) ? f - 4 : f;
+}
+
+__device__ __forceinline__ long plane_off(const DevGrid& g, int x, int y, int k) {
+  return ((long)wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
+}
+
+template <class T>
+__device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, int k, double* __restrict__ sDy,
+                                           double* __restrict__ sDz) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool valid = i < a.g.nx && j < a.g.ny;
   const Nbr n = make_nbr(a.g, i, j, k);
   const long fs = a.g.fstride;
+  const Coef& c = a.c;
+  double* __restrict__ D = a.D;
+  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+  // fields with first derivatives only: direct D1 and KO
+#pragma unroll 1
+  for (int m = 0; m < T::ND1; ++m) {
+    const int f = T::d1_field(m);
+    if (T::d2_slot(f) >= 0) continue;
+    const double* F = a.U + (long)f * fs;
+    if (valid) {
+      D[(long)(3 * m + 0) * fs + n.c] = fd1<0>(F, n, c);
+      D[(long)(3 * m + 1) * fs + n.c] = fd1<1>(F, n, c);
+      D[(long)(3 * m + 2) * fs + n.c] = fd1<2>(F, n, c);
+      D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko_add(F, n, c, ldg(F, n.c), 0.0);
+    }
+  }
+  // fields with second derivatives
+#pragma unroll 1
+  for (int m2 = 0; m2 < T::ND2; ++m2) {
+    const int f = T::d2_field(m2);
+    const double* F = a.U + (long)f * fs;
+    for (int q = tid; q < TXH * BY; q += BX * BY) {  // D_y on the x-extended tile
+      const int qx = q % TXH, qy = q / TXH;
+      const int x = i0 - 2 + qx, y = j0 + qy;
+      const double u = ldg(F, plane_off(a.g, x, y + 1, k)) - ldg(F, plane_off(a.g, x, y - 1, k));
+      const double v = ldg(F, plane_off(a.g, x, y + 2, k)) - ldg(F, plane_off(a.g, x, y - 2, k));
+      sDy[q] = u * c.d1a[1] - v * c.d1b[1];
+    }
+    for (int q = tid; q < TXH * (BY + 4); q += BX * BY) {  // D_z on the x- and y-extended tile
+      const int qx = q % TXH, qy = q / TXH;
+      const int x = i0 - 2 + qx, y = j0 - 2 + qy;
+      const double u = ldg(F, plane_off(a.g, x, y, k + 1)) - ldg(F, plane_off(a.g, x, y, k - 1));
+      const double v = ldg(F, plane_off(a.g, x, y, k + 2)) - ldg(F, plane_off(a.g, x, y, k - 2));
+      sDz[q] = u * c.d1a[2] - v * c.d1b[2];
+    }
+    __syncthreads();
+    if (valid) {
+      const double f0 = ldg(F, n.c);
+      double ko = 0.0, d2[3], d1x;
+      // x: neighbour differences shared by D1, D2 and KO
+      {
+        const double p1 = ldg(F, disp<0>(n, 1)) - f0, m1 = ldg(F, disp<0>(n, -1)) - f0;
+        const double p2 = ldg(F, disp<0>(n, 2)) - f0, m2v = ldg(F, disp<0>(n, -2)) - f0;
+        const double s3 = (ldg(F, disp<0>(n, 3)) - f0) + (ldg(F, disp<0>(n, -3)) - f0);
+        d1x = (p1 - m1) * c.d1a[0] - (p2 - m2v) * c.d1b[0];
+        const double s1 = p1 + m1, s2 = p2 + m2v;
+        d2[0] = s1 * c.d2a[0] - s2 * c.d2b[0];
+        ko = fma(c.ko[0], fma(15.0, s1, fma(-6.0, s2, s3)), ko);
+      }
+      {
+        const double s1 = (ldg(F, disp<1>(n, 1)) - f0) + (ldg(F, disp<1>(n, -1)) - f0);
+        const double s2 = (ldg(F, disp<1>(n, 2)) - f0) + (ldg(F, disp<1>(n, -2)) - f0);
+        const double s3 = (ldg(F, disp<1>(n, 3)) - f0) + (ldg(F, disp<1>(n, -3)) - f0);
+        d2[1] = s1 * c.d2a[1] - s2 * c.d2b[1];
+        ko = fma(c.ko[1], fma(15.0, s1, fma(-6.0, s2, s3)), ko);
+      }
+      {
+        const double s1 = (ldg(F, disp<2>(n, 1)) - f0) + (ldg(F, disp<2>(n, -1)) - f0);
+        const double s2 = (ldg(F, disp<2>(n, 2)) - f0) + (ldg(F, disp<2>(n, -2)) - f0);
+        const double s3 = (ldg(F, disp<2>(n, 3)) - f0) + (ldg(F, disp<2>(n, -3)) - f0);
+        d2[2] = s1 * c.d2a[2] - s2 * c.d2b[2];
+        ko = fma(c.ko[2], fma(15.0, s1, fma(-6.0, s2, s3)), ko);
+      }
+      const double* ry = sDy + ty * TXH + tx + 2;        // D_y at (i + o, j)
+      const double* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z at (i + o, j), row stride TXH along y
+      const double dxy = (ry[1] - ry[-1]) * c.d1a[0] - (ry[2] - ry[-2]) * c.d1b[0];
+      const double dxz = (rz[1] - rz[-1]) * c.d1a[0] - (rz[2] - rz[-2]) * c.d1b[0];
+      const double dyz = (rz[TXH] - rz[-TXH]) * c.d1a[1] - (rz[2 * TXH] - rz[-2 * TXH]) * c.d1b[1];
+      const int m1 = T::d1_slot(f);
+      D[(long)(3 * m1 + 0) * fs + n.c] = d1x;
+      D[(long)(3 * m1 + 1) * fs + n.c] = ry[0];
+      D[(long)(3 * m1 + 2) * fs + n.c] = rz[0];
+      const long b = (long)(3 * T::ND1 + 6 * m2) * fs + n.c;
+      D[b + 0 * fs] = d2[0];
+      D[b + 1 * fs] = dxy;
+      D[b + 2 * fs] = dxz;
+      D[b + 3 * fs] = d2[1];
+      D[b + 4 * fs] = dyz;
+      D[b + 5 * fs] = d2[2];
+      D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX* BY, COSMOS_DERIV_MIN_BLOCKS) deriv_kernel(const StageArgs a) {
+  __shared__ double sDy[TXH * BY], sDz[TXH * (BY + 4)];
+  deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * BY, blockIdx.z, sDy, sDz);
+}
+
+// Algebra pass at one grid point (i, j, k).
+template <class T, int MODE>
+__device__ __forceinline__ void alg_point(const StageArgs& a, const AlgebraParams& ap, int i, int j, int k) {
+  const long fs = a.g.fstride;
+  const long c = ((long)k * a.g.ny + j) * a.g.pitch + i;
+  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
   double in[T::NIN];
-  gather<T>(a.U, a.prim, n, a.c, fs, in);
+#pragma unroll
+  for (int f = 0; f < T::NF; ++f) in[f] = ldg(a.U + (long)f * fs, c);
+#pragma unroll
+  for (int m = 0; m < NDER0; ++m) in[T::NF + m] = ldg(a.D + (long)m * fs, c);
+  if constexpr (T::FLUID) in[T::NIN - 1] = ldg(a.prim, c);
   double out[T::NF];
   T::rhs(in, out, ap);
+  long cm[3] = {0, 0, 0};
+  if constexpr (T::FLUID) {
+    cm[0] = c - i + wrap_index(i - 1, a.g.nx);
+    cm[1] = c + (long)(wrap_index(j - 1, a.g.ny) - j) * a.g.pitch;
+    cm[2] = c + (long)(wrap_index(k - 1, a.g.nz) - k) * a.g.pitch * a.g.ny;
+  }
 #pragma unroll
   for (int f = 0; f < T::NF; ++f) {
     double r = out[f];
     if (T::FLUID && f >= 24 && f < 28) {
       const double* H = a.flux + (long)(f - 24) * fs;  // direction d at H + 4 d fs
-      r -= (ldg(H, n.c) - ldg(H, disp<0>(n, -1))) * a.c.ih[0];
-      r -= (ldg(H + 4 * fs, n.c) - ldg(H + 4 * fs, disp<1>(n, -1))) * a.c.ih[1];
-      r -= (ldg(H + 8 * fs, n.c) - ldg(H + 8 * fs, disp<2>(n, -1))) * a.c.ih[2];
+      r -= (ldg(H, c) - ldg(H, cm[0])) * a.c.ih[0];
+      r -= (ldg(H + 4 * fs, c) - ldg(H + 4 * fs, cm[1])) * a.c.ih[1];
+      r -= (ldg(H + 8 * fs, c) - ldg(H + 8 * fs, cm[2])) * a.c.ih[2];
     } else {
-      r = ko_add(a.U + (long)f * fs, n, a.c, in[f], r);
+      r += ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c);
     }
-    const long o = (long)f * fs + n.c;
+    const long o = (long)f * fs + c;
     if constexpr (MODE == MODE_RHS) {
       a.out[o] = r;
     } else if constexpr (MODE == MODE_S1) {
@@ -155,7 +294,7 @@ __global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS) stage_kernel(
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= a.g.nx || j >= a.g.ny) return;
-  stage_point<T, MODE>(a, a.ap, i, j, k);
+  alg_point<T, MODE>(a, a.ap, i, j, k);
 }
 
 // Point (i, j, k) of work item `t` (thread `lane` of the block) of a batch:
@@ -179,7 +318,18 @@ __device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g
   return true;
 }
 
-// Persistent batched stage kernel: blocks stride over the flat work list of
+// Persistent batched derivative pass over 32 x 4 tiles of every instance.
+template <class T>
+__global__ void __launch_bounds__(BX* BY, COSMOS_DERIV_MIN_BLOCKS) batch_deriv_kernel(const StageArgs* __restrict__ args,
+                                                             const BatchTile* __restrict__ tiles, long ntiles) {
+  __shared__ double sDy[TXH * BY], sDz[TXH * (BY + 4)];
+  for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+    const BatchTile t = tiles[w];
+    deriv_tile<T>(args[t.inst], t.a * BX, t.b * BY, t.c, sDy, sDz);
+  }
+}
+
+// Persistent batched algebra pass: blocks stride over the flat work list of
 // all instances; instance `inst` uses args[inst] with K_ref taken from kref.
 template <class T, int MODE>
 __global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS)
@@ -191,7 +341,7 @@ __global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS)
     AlgebraParams ap = a.ap;
     ap.Kref = kref[t.inst];
     int i, j, k;
-    if (batch_point(t, a.g, mapping, i, j, k)) stage_point<T, MODE>(a, ap, i, j, k);
+    if (batch_point(t, a.g, mapping, i, j, k)) alg_point<T, MODE>(a, ap, i, j, k);
   }
 }
 
@@ -258,6 +408,8 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
     static constexpr bool FLUID = IS_FLUID, SCALAR = IS_SCALAR;                                                 \
     __device__ static constexpr int d1_field(int m) { return alg_##NAME::d1_field(m); }                        \
     __device__ static constexpr int d2_field(int m) { return alg_##NAME::d2_field(m); }                        \
+    __device__ static constexpr int d1_slot(int f) { return alg_##NAME::d1_slot(f); }                          \
+    __device__ static constexpr int d2_slot(int f) { return alg_##NAME::d2_slot(f); }                          \
     __device__ static __forceinline__ void rhs(const double* in, double* out, const AlgebraParams& p) {          \
       alg_##NAME::rhs(in, out, p);                                                                              \
     }                                                                                                           \
@@ -267,7 +419,9 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   };                                                                                                            \
   cudaError_t launch_stage_##NAME(const StageArgs& a, int mode, cudaStream_t s) {                               \
     const dim3 grid = point_grid(a.g), block(BX, BY);                                                          \
-    switch (mode) {                                                                                             \
+    if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<grid, block, 0, s>>>(a);                             \
+    if (mode < 0) return cudaGetLastError();                                                                    \
+    switch (mode & 7) {                                                                                             \
       case MODE_RHS: stage_kernel<T_##NAME, MODE_RHS><<<grid, block, 0, s>>>(a); break;                        \
       case MODE_S1: stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(a); break;                          \
       case MODE_S23: stage_kernel<T_##NAME, MODE_S23><<<grid, block, 0, s>>>(a); break;                        \
@@ -276,7 +430,9 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
     return cudaGetLastError();                                                                                  \
   }                                                                                                             \
   cudaError_t launch_batch_stage_##NAME(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping,  \
-                                        const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s) {    \
+                                        const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s,      \
+                                        const BatchTile* dtiles, long ndtiles) {                                  \
+    batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, BY), 0, s>>>(args, dtiles, ndtiles);                          \
     switch (mode) {                                                                                             \
       case MODE_S1:                                                                                             \
         batch_stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \
