@@ -87,8 +87,21 @@ def scan_workload(args):
     from paper_2606_02053_gb300 import cosmos as C
     from paper_2606_02053_gb300.batch import BatchScan
 
-    build.build()
-    inst = inputs.scan_instances(args.instances, seed=2606)
+    from paper_2606_02053_gb300.dist import max_over_ranks, shard_instances, sum_over_ranks
+
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws_ > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    if rank == 0:
+        build.build()
+    if ws_ > 1:
+        tdist.barrier()
+    inst_all = inputs.scan_instances(args.instances, seed=2606)
+    mine = shard_instances([d["n"] ** 3 for d in inst_all], ws_)[rank]
+    inst = [inst_all[i] for i in mine]
     p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
     grids, dts, ids = [], [], []
     for d in inst:
@@ -112,7 +125,7 @@ def scan_workload(args):
         b.run(W, K, use_graph=True, stream=stream)
         e1.record(stream)
     torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) * 1e-3
+    t_batch = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
     # plain per-instance loop, same steps, one shared workspace
     nbmax = max(C.cosmos_workspace_bytes(g, p, C.COSMOS_OP_RK4) for g in grids)
     ws = torch.empty((nbmax + 7) // 8, dtype=torch.float64, device="cuda")
@@ -128,18 +141,21 @@ def scan_workload(args):
             C.check(C.cosmos_rk4_step(g, p, st, k * dt, dt, ws))
     f1.record()
     torch.cuda.synchronize()
-    t_loop = f0.elapsed_time(f1) * 1e-3
-    max_diff = max(float((a - c).abs().max()) for a, c in zip(b.states, loop_states))
+    t_loop = max_over_ranks(f0.elapsed_time(f1) * 1e-3)
+    max_diff = max_over_ranks(max(float((a - c).abs().max()) for a, c in zip(b.states, loop_states)))
+    total_pts = sum_over_ranks(total_pts)
     value = total_pts * K / t_batch
+    if rank != 0:
+        return
     line = {"metric": "batched threshold-scan FP64 grid-point RK4 updates/sec (64 instances, 64^3-96^3)",
-            "value": value, "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
-            "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "flrw_zeta_scan_64_instances_fluid_w1/3", "instances": len(grids),
-                       "points_total": int(total_pts), "grid_sizes": [g.nx for g in grids]},
+            "value": value, "unit": UNIT, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "n_gpus": ws_,
+            "config": {"workload": "flrw_zeta_scan_64_instances_fluid_w1/3", "instances": len(inst_all),
+                       "points_total": int(total_pts), "grid_sizes": [d["n"] for d in inst_all]},
             "per_instance_loop_value": total_pts * K / t_loop, "batched_speedup": t_loop / t_batch,
             "batched_vs_loop_max_abs_diff": max_diff, "autotune": tune,
-            "gpu_launches": K * 4 * 3}
+            "gpu_launches": K * 4 * 4}  # per stage: primitives, face fluxes, derivative, algebra passes
     print(json.dumps(line), flush=True)
 
 
@@ -403,10 +419,9 @@ def main():
     # pass_ms[pass][stage] = list over steps
     pass_ms = [[[ev_pairs[k][s][q][0].elapsed_time(ev_pairs[k][s][q][1]) for k in range(args.steps)] for s in range(4)]
                for q in range(2)]
-    if dist:
-        tt = torch.tensor([elapsed], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    from paper_2606_02053_gb300.dist import max_over_ranks
+
+    elapsed = max_over_ranks(elapsed)
     nranks = ws_
     pts = float(n) ** 3
     value = nranks * pts * args.steps / elapsed
@@ -425,12 +440,9 @@ def main():
     for k in range(e2e_steps):
         C.check(C.cosmos_evolve_host(g, p, host_in, host_out, dev, 1, k * dt, dt, ev.ws_rk4, stream))
     e2e_t = time.perf_counter() - t0
-    e2e = {"value": nranks * pts * e2e_steps / e2e_t if not dist else None, "unit": UNIT,
+    e2e = {"value": None, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
-    if dist:
-        tt = torch.tensor([e2e_t], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e["value"] = nranks * pts * e2e_steps / float(tt.item())
+    e2e["value"] = nranks * pts * e2e_steps / max_over_ranks(e2e_t)
 
     # ---- FP64 peak of this GPU (in-run DFMA probe) ----
     scratch = torch.empty(152 * 8 * 256, dtype=torch.float64, device=f"cuda:{local}")
@@ -444,7 +456,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         host_state = ev.get()
-        cpu = cpu_baseline_sample(n, planes=16, repeats=1, state=host_state)
+        cpu = cpu_baseline_sample(n, planes=n, repeats=1, state=host_state)
     # average launch duration per kernel (over the 4 stages and all steps)
     avg = {name: statistics.mean([x for st in pass_ms[q] for x in st]) * 1e-3
            for q, name in enumerate(["derivative", "algebra"])}
