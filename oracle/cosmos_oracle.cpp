@@ -11,8 +11,8 @@
  *   - Einstein equations G_{mu nu} = 8 pi T_{mu nu} (G = c = 1), with
  *     T = T^SC + T^FL, T^SC = d phi d phi - 1/2 g (d phi)^2,
  *     T^FL = (rho + P) u u + P g, P = w rho, box phi = 0, div T^FL = 0;
- *   - rewritten "as in the standard numerical-relativity textbooks" into the
- *     BSSN (chi-variant) 3+1 form, 4th-order centred finite differences,
+ *   - cast (the paper leaves this to standard numerical-relativity texts)
+ *     into the BSSN (chi-variant) 3+1 form, 4th-order centred finite differences,
  *     6th-derivative Kreiss-Oliger dissipation and classic RK4;
  *   - the fluid advanced with the Kurganov-Tadmor central scheme in a
  *     conservative (Shibata-Font lineage) 3+1 form;
