@@ -144,53 +144,65 @@ def algebra(fluid: bool, scalar: bool):
     Gu = []
     for k in range(3):
         Gu.append(Sym([gu[k, 0] * Gl[0][i, j] + gu[k, 1] * Gl[1][i, j] + gu[k, 2] * Gl[2][i, j] for (i, j) in PAIRS]))
-    Gd = [contract_sym(gu2, Gu[k]) for k in range(3)]
 
     # ---- conformal Ricci tensor ----
-    # C[k][m][i] = gt^ml Gamma^k_li
-    C = [[[gu[m, 0] * Gu[k][0, i] + gu[m, 1] * Gu[k][1, i] + gu[m, 2] * Gu[k][2, i] for i in range(3)]
-          for m in range(3)] for k in range(3)]
-    # T[i][j] = sum_km C[k][m][i] Gamma_jkm ;  U_ij = sum_kl C[k][l][i] Gamma_klj (symmetric)
-    T = [[None] * 3 for _ in range(3)]
+    # R_ij = -1/2 gt^lm d_l d_m gt_ij + gt_k(i d_j) Gt^k + Gd^k Gamma_(ij)k
+    #        + (T_ij + T_ji) + U_ij,
+    # T_ij = sum_km C[k][m][i] Gamma_jkm, U_ij = sum_kl C[k][l][i] Gamma_klj,
+    # C[k][m][i] = gt^ml Gamma^k_li.  The Christoffel products are accumulated
+    # into the six components index i by index i, so that only the nine
+    # C[.][.][i] of one i exist at a time (fewer values live at once).
+    acc = [None] * 6
+
+    def add_to(m, t):
+        acc[m] = t if acc[m] is None else acc[m] + t
+
     for i in range(3):
+        Ci = [[gu[m, 0] * Gu[k][0, i] + gu[m, 1] * Gu[k][1, i] + gu[m, 2] * Gu[k][2, i] for m in range(3)]
+              for k in range(3)]
         for j in range(3):
             s = None
             for k in range(3):
                 for m in range(3):
-                    t = C[k][m][i] * Gl[j][k, m]
+                    t = Ci[k][m] * Gl[j][k, m]
                     s = t if s is None else s + t
-            T[i][j] = s
-    # V[i][j] = gt_ki d_j Gt^k + Gd^k Gamma_ijk
-    V = [[None] * 3 for _ in range(3)]
-    for i in range(3):
-        for j in range(3):
-            s = None
-            for k in range(3):
-                t = gt[k, i] * dGt(j, k) + Gd[k] * Gl[i][j, k]
-                s = t if s is None else s + t
-            V[i][j] = s
-    Ric = []
-    for (i, j) in PAIRS:
-        U = None
+            add_to(PIDX[(i, j)], 2.0 * s if i == j else s)  # T_ij into R_ij (T_ii counted twice)
+            if j >= i:
+                u_ = None
+                for k in range(3):
+                    for l in range(3):
+                        t = Ci[k][l] * Gl[k][l, j]
+                        u_ = t if u_ is None else u_ + t
+                add_to(PIDX[(i, j)], u_)  # U_ij
+    Gd = [contract_sym(gu2, Gu[k]) for k in range(3)]
+    def V(i, j):  # gt_ki d_j Gt^k + Gd^k Gamma_ijk
+        s = None
         for k in range(3):
-            for l in range(3):
-                t = C[k][l][i] * Gl[k][l, j]
-                U = t if U is None else U + t
+            t = gt[k, i] * dGt(j, k) + Gd[k] * Gl[i][j, k]
+            s = t if s is None else s + t
+        return s
+
+    Ric = []
+    for m, (i, j) in enumerate(PAIRS):
         lap = None
-        for m, (l, n) in enumerate(PAIRS):
-            t = gu2[m] * ddgt(l, n, i, j)
+        for q, (l, n) in enumerate(PAIRS):
+            t = gu2[q] * ddgt(l, n, i, j)
             lap = t if lap is None else lap + t
-        if i == j:
-            sym_v = V[i][i]
-            tt = 2.0 * T[i][i]
-        else:
-            sym_v = 0.5 * (V[i][j] + V[j][i])
-            tt = T[i][j] + T[j][i]
-        Ric.append(-0.5 * lap + sym_v + tt + U)
+        sym_v = V(i, i) if i == j else 0.5 * (V(i, j) + V(j, i))
+        Ric.append(-0.5 * lap + sym_v + acc[m])
+    # the remaining uses of the second-kind Christoffels, formed here so that
+    # those 18 values die early
+    Gu_dchi = [Gu[0][i, j] * dchi[0] + Gu[1][i, j] * dchi[1] + Gu[2][i, j] * dchi[2] for (i, j) in PAIRS]
+    Gu_dal = [Gu[0][i, j] * dal[0] + Gu[1][i, j] * dal[1] + Gu[2][i, j] * dal[2] for (i, j) in PAIRS]
+    Aud = [[gu[i, 0] * At[0, j] + gu[i, 1] * At[1, j] + gu[i, 2] * At[2, j] for j in range(3)] for i in range(3)]
+    Atu = Sym([Aud[i][0] * gu[0, j] + Aud[i][1] * gu[1, j] + Aud[i][2] * gu[2, j] for (i, j) in PAIRS])
+    Atu2 = [Atu[a, b] * (1.0 if a == b else 2.0) for (a, b) in PAIRS]
+    GA = [contract_sym(Atu2, Gu[i]) for i in range(3)]
+
     # chi part: Rchi_ij = (DDchi_ij + gt_ij trDD)/(2chi) - d_i chi d_j chi/(4chi^2) - 3 gt_ij |dchi|^2/(4chi^2)
     wchi = [gu[l, 0] * dchi[0] + gu[l, 1] * dchi[1] + gu[l, 2] * dchi[2] for l in range(3)]  # gt^lm d_m chi
     dchi2 = wchi[0] * dchi[0] + wchi[1] * dchi[1] + wchi[2] * dchi[2]
-    DDchi = [dd(CHI, i, j) - (Gu[0][i, j] * dchi[0] + Gu[1][i, j] * dchi[1] + Gu[2][i, j] * dchi[2]) for (i, j) in PAIRS]
+    DDchi = [dd(CHI, i, j) - Gu_dchi[m] for m, (i, j) in enumerate(PAIRS)]
     trDD = contract_sym(gu2, Sym(DDchi))
     half_ichi = 0.5 * ichi
     q_ichi2 = 0.25 * ichi * ichi
@@ -202,17 +214,15 @@ def algebra(fluid: bool, scalar: bool):
     # ---- lapse derivatives ----
     dchi_dal = wchi[0] * dal[0] + wchi[1] * dal[1] + wchi[2] * dal[2]
     DDa = []
-    for (i, j) in PAIRS:
-        s = dd(ALP, i, j) - (Gu[0][i, j] * dal[0] + Gu[1][i, j] * dal[1] + Gu[2][i, j] * dal[2])
+    for m, (i, j) in enumerate(PAIRS):
+        s = dd(ALP, i, j) - Gu_dal[m]
         s = s + half_ichi * (dchi[i] * dal[j] + dchi[j] * dal[i] - gt[i, j] * dchi_dal)
         DDa.append(s)
     lap_a = chi * (contract_sym(gu2, Sym([dd(ALP, i, j) for (i, j) in PAIRS]))
                    - (Gd[0] * dal[0] + Gd[1] * dal[1] + Gd[2] * dal[2])) - 0.5 * dchi_dal
 
-    # ---- raised At ----
-    Aud = [[gu[i, 0] * At[0, j] + gu[i, 1] * At[1, j] + gu[i, 2] * At[2, j] for j in range(3)] for i in range(3)]
-    Atu = Sym([Aud[i][0] * gu[0, j] + Aud[i][1] * gu[1, j] + Aud[i][2] * gu[2, j] for (i, j) in PAIRS])
-    AA = contract_sym([Atu[i, j] * (1.0 if i == j else 2.0) for (i, j) in PAIRS], At)
+    # ---- raised At (Aud, Atu formed above) ----
+    AA = contract_sym(Atu2, At)
 
     # ---- matter ----
     rhoH = None
@@ -301,9 +311,8 @@ def algebra(fluid: bool, scalar: bool):
         s = s - (Gd[0] * dbeta(0, i) + Gd[1] * dbeta(1, i) + Gd[2] * dbeta(2, i))
         s = s + (2.0 / 3.0) * Gd[i] * divb
         s = s - 2.0 * (Atu[i, 0] * dal[0] + Atu[i, 1] * dal[1] + Atu[i, 2] * dal[2])
-        GA = contract_sym([Atu[a, b] * (1.0 if a == b else 2.0) for (a, b) in PAIRS], Gu[i])
         Adchi = Atu[i, 0] * dchi[0] + Atu[i, 1] * dchi[1] + Atu[i, 2] * dchi[2]
-        s = s + 2.0 * alpha * (GA - 1.5 * ichi * Adchi - (2.0 / 3.0) * gu_dK[i])
+        s = s + 2.0 * alpha * (GA[i] - 1.5 * ichi * Adchi - (2.0 / 3.0) * gu_dK[i])
         if have_matter:
             s = s - (16.0 * pi) * alpha * (gu[i, 0] * Jl[0] + gu[i, 1] * Jl[1] + gu[i, 2] * Jl[2])
         Gt_rhs.append(s)

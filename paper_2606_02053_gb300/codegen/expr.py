@@ -342,14 +342,29 @@ def op_counts(g: Graph, outputs: Sequence[Ex]) -> Dict[str, int]:
 
 def emit_function(g: Graph, fname: str, in_names: Sequence[str], out_exprs: Sequence[Ex], params: Sequence[str],
                   in_array="in", out_array="out", param_struct="p", qualifiers="__device__ __forceinline__",
-                  extra_args="") -> str:
+                  extra_args="", accessors=False, order=None) -> str:
     """Emit `void fname(const double* in, double* out, const ParamT& p)`.
 
-    in_names[i] is the input name stored at in[i]; outputs go to out[k]."""
+    in_names[i] is the input name stored at in[i]; outputs go to out[k].
+    With ``accessors`` the function is a template over the input and output
+    types (anything with ``in[i]`` and ``out[k] = v``, e.g. loads straight from
+    global memory and a store functor), and each output is written as soon as
+    its value exists.  ``order`` (a list of the reachable non-leaf nodes) fixes
+    the statement order; the default is creation (topological) order."""
     in_index = {nm: i for i, nm in enumerate(in_names)}
-    order = _reachable(g, [o.id for o in out_exprs])
+    reach = _reachable(g, [o.id for o in out_exprs])
+    if order is None:
+        order = reach
+    else:
+        leaves = [n for n in reach if g.ops[n] in ("in", "param", "const")]
+        assert sorted(order) == sorted(n for n in reach if g.ops[n] not in ("in", "param", "const"))
+        order = leaves + list(order)
+    outs_of: Dict[int, List[int]] = {}
+    for k, o in enumerate(out_exprs):
+        outs_of.setdefault(o.id, []).append(k)
     names: Dict[int, str] = {}
     lines = []
+    written = set()
     for n in order:
         op = g.ops[n]
         if op == "in":
@@ -365,9 +380,17 @@ def emit_function(g: Graph, fname: str, in_names: Sequence[str], out_exprs: Sequ
             t = f"t{n}"
             lines.append(f"  const double {t} = {_expr(g, n, lambda a: names[a])};")
             names[n] = t
+            if accessors:
+                for k in outs_of.get(n, []):
+                    lines.append(f"  {out_array}[{k}] = {t};")
+                    written.add(k)
     for k, o in enumerate(out_exprs):
-        lines.append(f"  {out_array}[{k}] = {names[o.id]};")
-    sig = f"{qualifiers} void {fname}(const double* __restrict__ {in_array}, double* __restrict__ {out_array}"
+        if k not in written:
+            lines.append(f"  {out_array}[{k}] = {names[o.id]};")
+    if accessors:
+        sig = (f"template <class In, class Out>\n{qualifiers} void {fname}(const In& {in_array}, Out&& {out_array}")
+    else:
+        sig = f"{qualifiers} void {fname}(const double* __restrict__ {in_array}, double* __restrict__ {out_array}"
     if params:
         sig += f", const {params[0]}& {param_struct}"
     sig += extra_args + ")"

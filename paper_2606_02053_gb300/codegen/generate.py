@@ -54,7 +54,7 @@ def render() -> dict:
         body.append(_table_fn("d2_field", L["d2"]))
         body.append(_slot_fn("d1_slot", L["d1"]))
         body.append(_slot_fn("d2_slot", L["d2"]))
-        body.append(emit_function(g, "rhs", L["names"], out, ["AlgebraParams"]))
+        body.append(emit_function(g, "rhs", L["names"], out, ["AlgebraParams"], accessors=True))
         body.append(emit_function(g, "constraints", L["names"], g.constraints, ["AlgebraParams"]))
         if name in ADJOINT_VARIANTS:
             # reverse mode: in[0 .. NIN) as for rhs, in[NIN + f] = cotangent of out[f];

@@ -47,7 +47,7 @@ struct BatchLayout {
 
 // 32 x 4 tiles of every plane: the derivative pass's work list
 static long deriv_tiles(const cosmos_grid& g) {
-  return (long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * g.nz;
+  return (long)((g.nx + BX - 1) / BX) * ((g.ny + DBY - 1) / DBY) * g.nz;
 }
 
 static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_params* p, int max_steps) {
@@ -95,7 +95,7 @@ struct cosmos_batch_s {
   long ntiles = 0, ndtiles = 0;
   StageArgs* d_args = nullptr;  // [4][n]
   BatchTile* d_tiles = nullptr;
-  BatchTile* d_dtiles = nullptr;  // derivative-pass tiles (32 x 4)
+  BatchTile* d_dtiles = nullptr;  // derivative-pass tiles (BX x DBY)
   double* d_kref = nullptr;     // [max_steps][4][n]
   cudaGraphExec_t gexec = nullptr;
   int g_first = -1, g_steps = -1;
@@ -246,7 +246,7 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
       for (int i = 0; i < n; ++i) {
         const cosmos_grid& g = grids[i];
         if (w >= deriv_tiles(g)) continue;
-        const int tx = (g.nx + BX - 1) / BX, ty = (g.ny + BY - 1) / BY;
+        const int tx = (g.nx + BX - 1) / BX, ty = (g.ny + DBY - 1) / DBY;
         dt.push_back(BatchTile{i, (int)(w % tx), (int)((w / tx) % ty), (int)(w / ((long)tx * ty))});
       }
     b->ndtiles = (long)dt.size();

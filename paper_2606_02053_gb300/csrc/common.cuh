@@ -13,6 +13,10 @@ namespace cosmos {
 constexpr double PI = 3.14159265358979323846;
 constexpr int BX = 32;  // threads per block along x (one warp = one row)
 constexpr int BY = 4;   // rows per block
+#ifndef COSMOS_DERIV_ROWS
+#define COSMOS_DERIV_ROWS 8
+#endif
+constexpr int DBY = COSMOS_DERIV_ROWS;  // rows per block of the derivative pass
 
 // Grid description as the kernels see it.
 struct DevGrid {
@@ -145,5 +149,6 @@ cudaError_t launch_fluid_flux(const DevGrid& g, const double* U, const double* p
                               int nf_offset_fluid, cudaStream_t s);
 
 inline dim3 point_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
+inline dim3 deriv_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, g.nz); }
 
 }  // namespace cosmos

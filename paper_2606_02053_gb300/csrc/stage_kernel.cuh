@@ -12,7 +12,10 @@
 #include "common.cuh"
 
 #ifndef COSMOS_DERIV_MIN_BLOCKS
-#define COSMOS_DERIV_MIN_BLOCKS 5  // derivative pass: resident 128-thread blocks per SM
+#define COSMOS_DERIV_MIN_BLOCKS 3  // derivative pass: resident blocks (of BX x DBY threads) per SM
+#endif
+#ifndef COSMOS_DERIV_STAGE_ALL
+#define COSMOS_DERIV_STAGE_ALL 0  // derivative pass: stage every second-derivative field behind one barrier
 #endif
 #ifndef COSMOS_STAGE_MIN_BLOCKS
 #define COSMOS_STAGE_MIN_BLOCKS 3  // resident 128-thread blocks per SM the register budget is sized for
@@ -88,6 +91,21 @@ __device__ __forceinline__ double ko_add(const double* __restrict__ F, const Nbr
   return r;
 }
 
+// Kreiss-Oliger term of a field on a grid with equal spacing along the three
+// axes (one coefficient c.ko[0]): the bracket is linear in s_k, so the three
+// axes are summed first, P_k = sum_d (f(+k e_d) + f(-k e_d)), and combined once:
+// (P3 - P2) - 5 (P2 - P1) + 10 (P1 - 6 f0).  For a constant field every P_k and
+// 6 f0 are the same single rounding of 6 f0, so each bracket is exactly zero.
+__device__ __forceinline__ double ko_uniform(const double* __restrict__ F, const Nbr& n, const Coef& c, double f0) {
+  double P[3];
+#pragma unroll
+  for (int k = 1; k <= 3; ++k)
+    P[k - 1] = ((ldg(F, disp<0>(n, k)) + ldg(F, disp<0>(n, -k))) + (ldg(F, disp<1>(n, k)) + ldg(F, disp<1>(n, -k)))) +
+               (ldg(F, disp<2>(n, k)) + ldg(F, disp<2>(n, -k)));
+  const double t = P[0] - __dmul_rn(6.0, f0);  // __dmul_rn: the product is rounded, never fused
+  return c.ko[0] * fma(10.0, t, fma(-5.0, P[1] - P[0], P[2] - P[1]));
+}
+
 // Inputs of the generated algebra at one point (layout documented in codegen/bssn.py).
 template <class T>
 __device__ __forceinline__ void gather(const double* __restrict__ U, const double* __restrict__ prim, const Nbr& n,
@@ -143,9 +161,101 @@ __device__ __forceinline__ long plane_off(const DevGrid& g, int x, int y, int k)
   return ((long)wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
 }
 
+// Shared-memory staging of the derivative pass: the y and z first derivatives
+// of the second-derivative fields on the tile plus halo, for one field at a
+// time (DERIV_STAGE_ALL = 0) or for all of them behind a single barrier (1).
+template <class T>
+struct DerivSmem {
+  static constexpr int NST = COSMOS_DERIV_STAGE_ALL ? T::ND2 : 1;
+  static constexpr int NY = TXH * DBY, NZ = TXH * (DBY + 4);  // doubles per staged field
+};
+
+// D_y (rows j0 .. j0+DBY-1) and D_z (rows j0-2 .. j0+DBY+1) of field F on the
+// x-extended tile into sDy / sDz.
+__device__ __forceinline__ void stage_dydz(const StageArgs& a, const double* __restrict__ F, int i0, int j0, int k,
+                                           int tid, double* __restrict__ sDy, double* __restrict__ sDz) {
+  const Coef& c = a.c;
+  for (int q = tid; q < TXH * DBY; q += BX * DBY) {
+    const int qx = q % TXH, qy = q / TXH;
+    const int x = i0 - 2 + qx, y = j0 + qy;
+    const double u = ldg(F, plane_off(a.g, x, y + 1, k)) - ldg(F, plane_off(a.g, x, y - 1, k));
+    const double v = ldg(F, plane_off(a.g, x, y + 2, k)) - ldg(F, plane_off(a.g, x, y - 2, k));
+    sDy[q] = u * c.d1a[1] - v * c.d1b[1];
+  }
+  for (int q = tid; q < TXH * (DBY + 4); q += BX * DBY) {
+    const int qx = q % TXH, qy = q / TXH;
+    const int x = i0 - 2 + qx, y = j0 - 2 + qy;
+    const double u = ldg(F, plane_off(a.g, x, y, k + 1)) - ldg(F, plane_off(a.g, x, y, k - 1));
+    const double v = ldg(F, plane_off(a.g, x, y, k + 2)) - ldg(F, plane_off(a.g, x, y, k - 2));
+    sDz[q] = u * c.d1a[2] - v * c.d1b[2];
+  }
+}
+
+// Everything the algebra needs from second-derivative field m2 at point n,
+// with its staged D_y / D_z.
+template <class T>
+__device__ __forceinline__ void deriv_d2_point(const StageArgs& a, int m2, const Nbr& n, int tx, int ty, bool ko_equal,
+                                               const double* __restrict__ sDy, const double* __restrict__ sDz) {
+  const long fs = a.g.fstride;
+  const Coef& c = a.c;
+  double* __restrict__ D = a.D;
+  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+  const int f = T::d2_field(m2);
+  const double* F = a.U + (long)f * fs;
+  const double f0 = ldg(F, n.c);
+  // per axis: s_k = (f(+k) - f0) + (f(-k) - f0) for k = 1, 2 (exact neighbour
+  // differences, shared by D2 and KO) and q3 = f(+3) + f(-3)
+  double d2[3], d1x, s1[3], s2[3], q3[3];
+  {
+    const double p1 = ldg(F, disp<0>(n, 1)) - f0, m1 = ldg(F, disp<0>(n, -1)) - f0;
+    const double p2 = ldg(F, disp<0>(n, 2)) - f0, m2v = ldg(F, disp<0>(n, -2)) - f0;
+    d1x = (p1 - m1) * c.d1a[0] - (p2 - m2v) * c.d1b[0];
+    s1[0] = p1 + m1;
+    s2[0] = p2 + m2v;
+    q3[0] = ldg(F, disp<0>(n, 3)) + ldg(F, disp<0>(n, -3));
+  }
+  s1[1] = (ldg(F, disp<1>(n, 1)) - f0) + (ldg(F, disp<1>(n, -1)) - f0);
+  s2[1] = (ldg(F, disp<1>(n, 2)) - f0) + (ldg(F, disp<1>(n, -2)) - f0);
+  q3[1] = ldg(F, disp<1>(n, 3)) + ldg(F, disp<1>(n, -3));
+  s1[2] = (ldg(F, disp<2>(n, 1)) - f0) + (ldg(F, disp<2>(n, -1)) - f0);
+  s2[2] = (ldg(F, disp<2>(n, 2)) - f0) + (ldg(F, disp<2>(n, -2)) - f0);
+  q3[2] = ldg(F, disp<2>(n, 3)) + ldg(F, disp<2>(n, -3));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) d2[d] = s1[d] * c.d2a[d] - s2[d] * c.d2b[d];
+  // KO bracket per axis: (q3 - 2 f0) - 6 s2 + 15 s1, exactly zero for constants
+  double ko;
+  if (ko_equal) {
+    const double Q3 = ((q3[0] + q3[1]) + q3[2]) - __dmul_rn(6.0, f0);
+    ko = c.ko[0] * fma(15.0, (s1[0] + s1[1]) + s1[2], fma(-6.0, (s2[0] + s2[1]) + s2[2], Q3));
+  } else {
+    ko = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ko = fma(c.ko[d], fma(15.0, s1[d], fma(-6.0, s2[d], q3[d] - 2.0 * f0)), ko);
+  }
+  const double* ry = sDy + ty * TXH + tx + 2;        // D_y at (i + o, j)
+  const double* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z at (i + o, j), row stride TXH along y
+  const double dxy = (ry[1] - ry[-1]) * c.d1a[0] - (ry[2] - ry[-2]) * c.d1b[0];
+  const double dxz = (rz[1] - rz[-1]) * c.d1a[0] - (rz[2] - rz[-2]) * c.d1b[0];
+  const double dyz = (rz[TXH] - rz[-TXH]) * c.d1a[1] - (rz[2 * TXH] - rz[-2 * TXH]) * c.d1b[1];
+  const int m1 = T::d1_slot(f);
+  D[(long)(3 * m1 + 0) * fs + n.c] = d1x;
+  D[(long)(3 * m1 + 1) * fs + n.c] = ry[0];
+  D[(long)(3 * m1 + 2) * fs + n.c] = rz[0];
+  const long b = (long)(3 * T::ND1 + 6 * m2) * fs + n.c;
+  D[b + 0 * fs] = d2[0];
+  D[b + 1 * fs] = dxy;
+  D[b + 2 * fs] = dxz;
+  D[b + 3 * fs] = d2[1];
+  D[b + 4 * fs] = dyz;
+  D[b + 5 * fs] = d2[2];
+  D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko;
+}
+
+// One BX x DBY tile of z-plane k (block of BX x DBY threads).
 template <class T>
 __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, int k, double* __restrict__ sDy,
                                            double* __restrict__ sDz) {
+  using S = DerivSmem<T>;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int i = i0 + tx, j = j0 + ty;
   const bool valid = i < a.g.nx && j < a.g.ny;
@@ -154,6 +264,12 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
   const Coef& c = a.c;
   double* __restrict__ D = a.D;
   constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+  const bool ko_equal = c.ko[0] == c.ko[1] && c.ko[1] == c.ko[2];  // same for every thread
+  if constexpr (S::NST > 1) {
+#pragma unroll 1
+    for (int m2 = 0; m2 < T::ND2; ++m2)
+      stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy + m2 * S::NY, sDz + m2 * S::NZ);
+  }
   // fields with first derivatives only: direct D1 and KO
 #pragma unroll 1
   for (int m = 0; m < T::ND1; ++m) {
@@ -164,128 +280,105 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
       D[(long)(3 * m + 0) * fs + n.c] = fd1<0>(F, n, c);
       D[(long)(3 * m + 1) * fs + n.c] = fd1<1>(F, n, c);
       D[(long)(3 * m + 2) * fs + n.c] = fd1<2>(F, n, c);
-      D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko_add(F, n, c, ldg(F, n.c), 0.0);
+      D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] =
+          ko_equal ? ko_uniform(F, n, c, ldg(F, n.c)) : ko_add(F, n, c, ldg(F, n.c), 0.0);
     }
   }
   // fields with second derivatives
-#pragma unroll 1
-  for (int m2 = 0; m2 < T::ND2; ++m2) {
-    const int f = T::d2_field(m2);
-    const double* F = a.U + (long)f * fs;
-    for (int q = tid; q < TXH * BY; q += BX * BY) {  // D_y on the x-extended tile
-      const int qx = q % TXH, qy = q / TXH;
-      const int x = i0 - 2 + qx, y = j0 + qy;
-      const double u = ldg(F, plane_off(a.g, x, y + 1, k)) - ldg(F, plane_off(a.g, x, y - 1, k));
-      const double v = ldg(F, plane_off(a.g, x, y + 2, k)) - ldg(F, plane_off(a.g, x, y - 2, k));
-      sDy[q] = u * c.d1a[1] - v * c.d1b[1];
-    }
-    for (int q = tid; q < TXH * (BY + 4); q += BX * BY) {  // D_z on the x- and y-extended tile
-      const int qx = q % TXH, qy = q / TXH;
-      const int x = i0 - 2 + qx, y = j0 - 2 + qy;
-      const double u = ldg(F, plane_off(a.g, x, y, k + 1)) - ldg(F, plane_off(a.g, x, y, k - 1));
-      const double v = ldg(F, plane_off(a.g, x, y, k + 2)) - ldg(F, plane_off(a.g, x, y, k - 2));
-      sDz[q] = u * c.d1a[2] - v * c.d1b[2];
-    }
+  if constexpr (S::NST > 1) {
     __syncthreads();
     if (valid) {
-      const double f0 = ldg(F, n.c);
-      double ko = 0.0, d2[3], d1x;
-      // x: neighbour differences shared by D1, D2 and KO
-      {
-        const double p1 = ldg(F, disp<0>(n, 1)) - f0, m1 = ldg(F, disp<0>(n, -1)) - f0;
-        const double p2 = ldg(F, disp<0>(n, 2)) - f0, m2v = ldg(F, disp<0>(n, -2)) - f0;
-        const double s3 = (ldg(F, disp<0>(n, 3)) - f0) + (ldg(F, disp<0>(n, -3)) - f0);
-        d1x = (p1 - m1) * c.d1a[0] - (p2 - m2v) * c.d1b[0];
-        const double s1 = p1 + m1, s2 = p2 + m2v;
-        d2[0] = s1 * c.d2a[0] - s2 * c.d2b[0];
-        ko = fma(c.ko[0], fma(15.0, s1, fma(-6.0, s2, s3)), ko);
-      }
-      {
-        const double s1 = (ldg(F, disp<1>(n, 1)) - f0) + (ldg(F, disp<1>(n, -1)) - f0);
-        const double s2 = (ldg(F, disp<1>(n, 2)) - f0) + (ldg(F, disp<1>(n, -2)) - f0);
-        const double s3 = (ldg(F, disp<1>(n, 3)) - f0) + (ldg(F, disp<1>(n, -3)) - f0);
-        d2[1] = s1 * c.d2a[1] - s2 * c.d2b[1];
-        ko = fma(c.ko[1], fma(15.0, s1, fma(-6.0, s2, s3)), ko);
-      }
-      {
-        const double s1 = (ldg(F, disp<2>(n, 1)) - f0) + (ldg(F, disp<2>(n, -1)) - f0);
-        const double s2 = (ldg(F, disp<2>(n, 2)) - f0) + (ldg(F, disp<2>(n, -2)) - f0);
-        const double s3 = (ldg(F, disp<2>(n, 3)) - f0) + (ldg(F, disp<2>(n, -3)) - f0);
-        d2[2] = s1 * c.d2a[2] - s2 * c.d2b[2];
-        ko = fma(c.ko[2], fma(15.0, s1, fma(-6.0, s2, s3)), ko);
-      }
-      const double* ry = sDy + ty * TXH + tx + 2;        // D_y at (i + o, j)
-      const double* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z at (i + o, j), row stride TXH along y
-      const double dxy = (ry[1] - ry[-1]) * c.d1a[0] - (ry[2] - ry[-2]) * c.d1b[0];
-      const double dxz = (rz[1] - rz[-1]) * c.d1a[0] - (rz[2] - rz[-2]) * c.d1b[0];
-      const double dyz = (rz[TXH] - rz[-TXH]) * c.d1a[1] - (rz[2 * TXH] - rz[-2 * TXH]) * c.d1b[1];
-      const int m1 = T::d1_slot(f);
-      D[(long)(3 * m1 + 0) * fs + n.c] = d1x;
-      D[(long)(3 * m1 + 1) * fs + n.c] = ry[0];
-      D[(long)(3 * m1 + 2) * fs + n.c] = rz[0];
-      const long b = (long)(3 * T::ND1 + 6 * m2) * fs + n.c;
-      D[b + 0 * fs] = d2[0];
-      D[b + 1 * fs] = dxy;
-      D[b + 2 * fs] = dxz;
-      D[b + 3 * fs] = d2[1];
-      D[b + 4 * fs] = dyz;
-      D[b + 5 * fs] = d2[2];
-      D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko;
+#pragma unroll 1
+      for (int m2 = 0; m2 < T::ND2; ++m2) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy + m2 * S::NY, sDz + m2 * S::NZ);
     }
-    __syncthreads();
+    __syncthreads();  // the staging area is reused by the block's next tile
+  } else {
+#pragma unroll 1
+    for (int m2 = 0; m2 < T::ND2; ++m2) {
+      stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy, sDz);
+      __syncthreads();
+      if (valid) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy, sDz);
+      __syncthreads();
+    }
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(BX* BY, COSMOS_DERIV_MIN_BLOCKS) deriv_kernel(const StageArgs a) {
-  __shared__ double sDy[TXH * BY], sDz[TXH * (BY + 4)];
-  deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * BY, blockIdx.z, sDy, sDz);
+__global__ void __launch_bounds__(BX* DBY, COSMOS_DERIV_MIN_BLOCKS) deriv_kernel(const StageArgs a) {
+  __shared__ double sDy[DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DerivSmem<T>::NST * DerivSmem<T>::NZ];
+  deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
 }
+
+// Inputs of the algebra pass at one point, read from global memory where the
+// generated code uses them (state values, then the derivative buffer, then the
+// fluid density), so that no input has to stay live in a register.
+template <class T>
+struct AlgIn {
+  const double* __restrict__ U;
+  const double* __restrict__ D;
+  const double* __restrict__ prim;
+  long fs, c;
+  __device__ __forceinline__ double operator[](int k) const {
+    constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+    if (k < T::NF) return ldg(U + (long)k * fs, c);
+    if (k < T::NF + NDER0) return ldg(D + (long)(k - T::NF) * fs, c);
+    return ldg(prim, c);
+  }
+};
+
+// Output side of the algebra pass: out[f] = r adds the Kreiss-Oliger term (or
+// the fluid flux divergence) and applies the RK4 stage combine of MODE, as
+// soon as the generated code has the value.
+template <class T, int MODE>
+struct AlgOut {
+  const StageArgs& a;
+  long fs, c;
+  long cm[3];
+  struct Slot {
+    const AlgOut& o;
+    int f;
+    __device__ __forceinline__ void operator=(double r) const {
+      const StageArgs& a = o.a;
+      const long fs = o.fs, c = o.c;
+      constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+      if (T::FLUID && f >= 24 && f < 28) {
+        const double* H = a.flux + (long)(f - 24) * fs;  // direction d at H + 4 d fs
+        r -= (ldg(H, c) - ldg(H, o.cm[0])) * a.c.ih[0];
+        r -= (ldg(H + 4 * fs, c) - ldg(H + 4 * fs, o.cm[1])) * a.c.ih[1];
+        r -= (ldg(H + 8 * fs, c) - ldg(H + 8 * fs, o.cm[2])) * a.c.ih[2];
+      } else {
+        r += ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c);
+      }
+      const long ofs = (long)f * fs + c;
+      if constexpr (MODE == MODE_RHS) {
+        a.out[ofs] = r;
+      } else if constexpr (MODE == MODE_S1) {
+        a.out[ofs] = fma(a.cdt, r, ldg(a.U0, ofs));
+        a.acc[ofs] = r;
+      } else if constexpr (MODE == MODE_S23) {
+        a.out[ofs] = fma(a.cdt, r, ldg(a.U0, ofs));
+        a.acc[ofs] = fma(a.bk, r, a.acc[ofs]);
+      } else {
+        a.U0w[ofs] = fma(a.cdt, a.acc[ofs] + r, a.U0w[ofs]);
+      }
+    }
+  };
+  __device__ __forceinline__ Slot operator[](int f) const { return Slot{*this, f}; }
+};
 
 // Algebra pass at one grid point (i, j, k).
 template <class T, int MODE>
 __device__ __forceinline__ void alg_point(const StageArgs& a, const AlgebraParams& ap, int i, int j, int k) {
   const long fs = a.g.fstride;
   const long c = ((long)k * a.g.ny + j) * a.g.pitch + i;
-  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
-  double in[T::NIN];
-#pragma unroll
-  for (int f = 0; f < T::NF; ++f) in[f] = ldg(a.U + (long)f * fs, c);
-#pragma unroll
-  for (int m = 0; m < NDER0; ++m) in[T::NF + m] = ldg(a.D + (long)m * fs, c);
-  if constexpr (T::FLUID) in[T::NIN - 1] = ldg(a.prim, c);
-  double out[T::NF];
-  T::rhs(in, out, ap);
-  long cm[3] = {0, 0, 0};
+  const AlgIn<T> in{a.U, a.D, a.prim, fs, c};
+  AlgOut<T, MODE> out{a, fs, c, {0, 0, 0}};
   if constexpr (T::FLUID) {
-    cm[0] = c - i + wrap_index(i - 1, a.g.nx);
-    cm[1] = c + (long)(wrap_index(j - 1, a.g.ny) - j) * a.g.pitch;
-    cm[2] = c + (long)(wrap_index(k - 1, a.g.nz) - k) * a.g.pitch * a.g.ny;
+    out.cm[0] = c - i + wrap_index(i - 1, a.g.nx);
+    out.cm[1] = c + (long)(wrap_index(j - 1, a.g.ny) - j) * a.g.pitch;
+    out.cm[2] = c + (long)(wrap_index(k - 1, a.g.nz) - k) * a.g.pitch * a.g.ny;
   }
-#pragma unroll
-  for (int f = 0; f < T::NF; ++f) {
-    double r = out[f];
-    if (T::FLUID && f >= 24 && f < 28) {
-      const double* H = a.flux + (long)(f - 24) * fs;  // direction d at H + 4 d fs
-      r -= (ldg(H, c) - ldg(H, cm[0])) * a.c.ih[0];
-      r -= (ldg(H + 4 * fs, c) - ldg(H + 4 * fs, cm[1])) * a.c.ih[1];
-      r -= (ldg(H + 8 * fs, c) - ldg(H + 8 * fs, cm[2])) * a.c.ih[2];
-    } else {
-      r += ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c);
-    }
-    const long o = (long)f * fs + c;
-    if constexpr (MODE == MODE_RHS) {
-      a.out[o] = r;
-    } else if constexpr (MODE == MODE_S1) {
-      a.out[o] = fma(a.cdt, r, ldg(a.U0, o));
-      a.acc[o] = r;
-    } else if constexpr (MODE == MODE_S23) {
-      a.out[o] = fma(a.cdt, r, ldg(a.U0, o));
-      a.acc[o] = fma(a.bk, r, a.acc[o]);
-    } else {
-      a.U0w[o] = fma(a.cdt, a.acc[o] + r, a.U0w[o]);
-    }
-  }
+  T::rhs(in, out, ap);
 }
 
 template <class T, int MODE>
@@ -320,12 +413,12 @@ __device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g
 
 // Persistent batched derivative pass over 32 x 4 tiles of every instance.
 template <class T>
-__global__ void __launch_bounds__(BX* BY, COSMOS_DERIV_MIN_BLOCKS) batch_deriv_kernel(const StageArgs* __restrict__ args,
-                                                             const BatchTile* __restrict__ tiles, long ntiles) {
-  __shared__ double sDy[TXH * BY], sDz[TXH * (BY + 4)];
+__global__ void __launch_bounds__(BX* DBY, COSMOS_DERIV_MIN_BLOCKS) batch_deriv_kernel(const StageArgs* __restrict__ args,
+                                                              const BatchTile* __restrict__ tiles, long ntiles) {
+  __shared__ double sDy[DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DerivSmem<T>::NST * DerivSmem<T>::NZ];
   for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
     const BatchTile t = tiles[w];
-    deriv_tile<T>(args[t.inst], t.a * BX, t.b * BY, t.c, sDy, sDz);
+    deriv_tile<T>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);
   }
 }
 
@@ -410,7 +503,8 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
     __device__ static constexpr int d2_field(int m) { return alg_##NAME::d2_field(m); }                        \
     __device__ static constexpr int d1_slot(int f) { return alg_##NAME::d1_slot(f); }                          \
     __device__ static constexpr int d2_slot(int f) { return alg_##NAME::d2_slot(f); }                          \
-    __device__ static __forceinline__ void rhs(const double* in, double* out, const AlgebraParams& p) {          \
+    template <class In, class Out>                                                                              \
+    __device__ static __forceinline__ void rhs(const In& in, Out&& out, const AlgebraParams& p) {               \
       alg_##NAME::rhs(in, out, p);                                                                              \
     }                                                                                                           \
     __device__ static __forceinline__ void constraints(const double* in, double* out, const AlgebraParams& p) {  \
@@ -419,7 +513,7 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   };                                                                                                            \
   cudaError_t launch_stage_##NAME(const StageArgs& a, int mode, cudaStream_t s) {                               \
     const dim3 grid = point_grid(a.g), block(BX, BY);                                                          \
-    if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<grid, block, 0, s>>>(a);                             \
+    if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);         \
     if (mode < 0) return cudaGetLastError();                                                                    \
     switch (mode & 7) {                                                                                             \
       case MODE_RHS: stage_kernel<T_##NAME, MODE_RHS><<<grid, block, 0, s>>>(a); break;                        \
@@ -432,7 +526,7 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   cudaError_t launch_batch_stage_##NAME(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping,  \
                                         const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s,      \
                                         const BatchTile* dtiles, long ndtiles) {                                  \
-    batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, BY), 0, s>>>(args, dtiles, ndtiles);                          \
+    batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);                         \
     switch (mode) {                                                                                             \
       case MODE_S1:                                                                                             \
         batch_stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \

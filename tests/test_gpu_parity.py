@@ -87,6 +87,34 @@ def test_rhs_parity_thin_and_tiny_grids(C, O):
         assert field_errors(r, ref).max() <= RHS_TOL, n
 
 
+@pytest.mark.parametrize("fluid,scalar", [(0, 0), (1, 1)])
+def test_rhs_parity_anisotropic_spacing(C, O, fluid, scalar):
+    """Unequal h along the axes: the derivative pass takes its per-axis
+    Kreiss-Oliger branch (equal spacing sums the axes first)."""
+    from paper_2606_02053_gb300 import inputs
+
+    n = (21, 14, 10)
+    h = (1.0 / 21, 1.3 / 14, 0.9 / 10)
+    p = C.make_params(slicing=0, shift=1, fluid=fluid, scalar=scalar, eta=1.1, ko_sigma=0.25, H0=2.0 * fluid)
+    s = inputs.smooth_state(n, seed=31 + fluid, fluid=fluid, scalar=scalar)
+    r, ref = run_rhs(C, O, n, h, p, s, t=0.02)
+    assert field_errors(r, ref).max() <= RHS_TOL
+
+
+@pytest.mark.parametrize("h", [0.1, (0.1, 0.07, 0.13)])
+def test_flat_space_rhs_is_exactly_zero_both_ko_branches(C, O, h):
+    n = (12, 9, 7)
+    p = C.make_params(ko_sigma=0.3)
+    s = np.zeros((24, n[2], n[1], n[0]))
+    s[0] = 0.7
+    s[1] = s[4] = s[6] = 1.0
+    s[17] = 1.3
+    s[18] = 0.2
+    s[19] = -0.45
+    r, _ = run_rhs(C, O, n, h, p, s)
+    assert np.all(r == 0.0)
+
+
 def test_flat_space_rhs_is_exactly_zero(C, O):
     n = (12, 9, 7)
     p = C.make_params()
