@@ -1,0 +1,172 @@
+"""Parity at the full sizes of the benchmark workloads, on the GPU.
+
+The oracle cannot evolve a 256^3 or 128^3 grid for hundreds of steps in a
+test, so each full-size run is checked by what the oracle can compute one by
+one and by properties that hold at any size:
+
+* 256^3 gauge wave (1+log slicing, Gamma-driver shift, A = 0.01, dt = h/4),
+  100 RK4 steps through the same kernels and launch shapes as the bench: the
+  data depend on x alone, so the oracle evolves the n x 1 x 1 line (the y and z
+  differences vanish exactly on both sides) and every (y, z) row must match it;
+* one right-hand side of a generic smooth state at 256^3, sampled at interior,
+  face, edge and corner points against the oracle's per-point right-hand side;
+* 128^3 radiation FLRW + Gaussian zeta (mu = 0.5, sigma = L/8, H0 L = 40),
+  200 RK4 steps: constraint norms reported, the symmetry of the data under
+  axis permutations and reflections kept to rounding, and the right-hand side
+  of the evolved state sampled against the oracle.
+
+Tolerances as in test_gpu_parity: 1e-12 per right-hand side, 1e-10 after steps.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-12
+STEP_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2606_02053_gb300 import build, cosmos
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    cosmos.lib()
+    return cosmos
+
+
+def oracle_params(O, Cp):
+    return O.params_array(slicing=Cp.slicing, shift=Cp.shift, eta=Cp.eta, ko_sigma=Cp.ko_sigma, w=Cp.w,
+                          fluid=Cp.fluid, scalar=Cp.scalar, H0=Cp.H0, t0=Cp.t0)
+
+
+def sample_points(n, count, seed):
+    """Random points plus every corner, edge midpoint and face centre (periodic wrap)."""
+    rng = np.random.default_rng(seed)
+    pts = [rng.integers(0, n, size=3) for _ in range(count)]
+    ends = [0, 1, 2, n // 2, n - 3, n - 2, n - 1]
+    for a in ends:
+        for b in ends:
+            pts += [(a, b, 0), (a, 0, b), (0, a, b), (a, b, n - 1), (a, n - 1, b), (n - 1, a, b)]
+    return np.unique(np.array(pts, dtype=np.int64).reshape(-1, 3), axis=0)
+
+
+def sampled_rhs_errors(gpu_rhs, ref, pts):
+    """gpu_rhs [nf, nz, ny, nx], ref [npts, nf] at (i, j, k) points; per-field relative errors."""
+    g = gpu_rhs[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    floor = 1e-12 * np.abs(ref).max()
+    den = np.maximum(np.abs(ref).max(axis=0), floor)
+    return np.abs(g - ref).max(axis=0) / den
+
+
+def test_gauge_wave_256_cube_100_steps(C, O):
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n, h = 256, 1.0 / 256
+    steps = 100
+    p = C.make_params(slicing=0, shift=1, eta=2.0, ko_sigma=0.1)
+    ev = Evolution(C.make_grid(n, h), p)
+    ev.init(C.make_id(0, A=0.01))
+    ev.step(0.0, 0.25 * h, steps=steps)
+    g = ev.view()[..., :n]
+    row = g[:, :1, :1, :]
+    assert float((g - row).abs().max()) <= 1e-13  # y, z invariance kept at full size
+    samples = g[:, [0, 17, 128, 255], :, :][:, :, [0, 101, 255], :].cpu().numpy()
+    del ev, g, row
+    torch.cuda.empty_cache()
+    op = oracle_params(O, p)
+    ot = O.OGrid((n, 1, 1), h)
+    ref = O.init(ot, op, O.id_array(0, A=0.01))
+    O.evolve(ot, op, ref, 0.0, 0.25 * h, steps)
+    ref = ref.reshape(ref.shape[0], n)
+    floor = 1e-12 * np.abs(ref).max()
+    den = np.maximum(np.abs(ref).max(axis=1), floor)
+    err = (np.abs(samples - ref[:, None, None, :]).max(axis=(1, 2, 3))) / den
+    assert err.max() <= STEP_TOL, err
+
+
+def test_rhs_sampled_parity_generic_state_256(C, O):
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n, h = 256, 1.0 / 256
+    p = C.make_params(slicing=0, shift=1, eta=2.0, ko_sigma=0.1)
+    s = inputs.smooth_state(n, seed=2561, kmax=6, scale=0.5)
+    ev = Evolution(C.make_grid(n, h), p)
+    ev.set_state(s)
+    r = ev.get(ev.rhs(0.0))
+    del ev
+    torch.cuda.empty_cache()
+    pts = sample_points(n, 1500, seed=17)
+    ref = O.rhs_points(O.OGrid((n, n, n), h), oracle_params(O, p), s, pts, 0.0)
+    err = sampled_rhs_errors(r, ref, pts)
+    assert err.max() <= RHS_TOL, (err.argmax(), err.max())
+
+
+def test_flrw_zeta_128_cube_200_steps(C, O):
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = 128
+    h = 1.0 / n
+    x0 = (-(n // 2) * h,) * 3
+    p = C.make_params(fluid=1, w=1.0 / 3.0, H0=40.0)
+    ev = Evolution(C.make_grid(n, h, x0=x0), p)
+    ev.init(C.make_id(1, mu=0.5, sigma=0.125))
+    _, norms0 = ev.constraints()
+    dt = 0.25 * h
+    ev.step(0.0, dt, steps=200)
+    _, norms = ev.constraints()
+    print(f"\n128^3 FLRW+zeta: constraint norms at t=0 {norms0.tolist()}\n  after 200 steps {norms.tolist()}")
+    assert np.all(np.isfinite(norms))
+    # initial data: H vanishes to rounding (relative to the background 6 H0^2 scale), M exactly
+    assert norms0[4] <= 1e-12 * 6.0 * 40.0 ** 2 and norms0[5:].max() == 0.0
+    s = ev.get()
+    # the data are symmetric about the centre c = n/2 under x <-> y and x -> 2c - x;
+    # fields map as tensors (chi, K, alpha, tau scalars; gt_xx <-> gt_yy, ...)
+    c = n // 2
+    swap = s.transpose(0, 1, 3, 2)  # x <-> y on [f, z, y, x]
+    perm = [0, 4, 2, 5, 1, 3, 6, 7, 11, 9, 12, 8, 10, 13, 15, 14, 16, 17, 19, 18, 20, 22, 21, 23, 24, 26, 25, 27]
+    scale = np.maximum(np.abs(s).reshape(s.shape[0], -1).max(axis=1), 1e-8 * np.abs(s).max())
+    err_swap = np.abs(swap[perm] - s).reshape(s.shape[0], -1).max(axis=1) / scale
+    assert err_swap.max() <= 1e-10, err_swap
+    refl = np.roll(s[..., ::-1], 2 * c + 1 - n, axis=3)  # x -> 2c - x (periodic)
+    sign = np.ones(s.shape[0])
+    for f in (2, 3, 9, 10, 14, 18, 21, 25):  # odd under x -> -x: gt_xy, gt_xz, At_xy, At_xz, Gt^x, beta^x, B^x, S_x
+        sign[f] = -1.0
+    err_refl = np.abs(sign[:, None, None, None] * refl - s).reshape(s.shape[0], -1).max(axis=1) / scale
+    assert err_refl.max() <= 1e-10, err_refl
+    r = ev.get(ev.rhs(200 * dt))
+    del ev
+    torch.cuda.empty_cache()
+    pts = sample_points(n, 1000, seed=29)
+    ref = O.rhs_points(O.OGrid((n, n, n), h, x0=x0), oracle_params(O, p), s, pts, 200 * dt)
+    err = sampled_rhs_errors(r, ref, pts)
+    assert err.max() <= RHS_TOL, (err.argmax(), err.max())
+
+
+def test_flrw_zeta_32_cube_200_steps_vs_oracle(C, O):
+    """The same physics and end time as the 128^3 run (t = 200 h_128 / 4), at a size
+    the oracle evolves, in the same 200 RK4 steps (dt = h_32 / 16)."""
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = 32
+    h = 1.0 / n
+    x0 = (-(n // 2) * h,) * 3
+    p = C.make_params(fluid=1, w=1.0 / 3.0, H0=40.0)
+    ev = Evolution(C.make_grid(n, h, x0=x0), p)
+    ev.init(C.make_id(1, mu=0.5, sigma=0.125))
+    og = O.OGrid((n, n, n), h, x0=x0)
+    op = oracle_params(O, p)
+    ref = O.init(og, op, O.id_array(1, mu=0.5, sigma=0.125))
+    dt = h / 16
+    ev.step(0.0, dt, steps=200)
+    O.evolve(og, op, ref, 0.0, dt, 200)
+    g = ev.get()
+    floor = 1e-12 * np.abs(ref).max()
+    den = np.maximum(np.abs(ref).reshape(ref.shape[0], -1).max(axis=1), floor)
+    err = np.abs(g - ref).reshape(ref.shape[0], -1).max(axis=1) / den
+    assert err.max() <= STEP_TOL, err
