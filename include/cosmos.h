@@ -152,8 +152,16 @@ int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state,
                     size_t ws_bytes, void* stream);
 
 /* End-to-end step with HOST buffers: copies host_in (pageable or pinned
- * host memory, cosmos_field_stride * nfields doubles) to dev_state, runs
- * `steps` RK4 steps and copies the result to host_out; synchronous. */
+ * host memory, cosmos_field_stride * nfields doubles, library layout) to
+ * dev_state, runs `steps` RK4 steps (ws: COSMOS_OP_RK4 bytes) and copies the
+ * result to host_out; synchronous.  host_in and host_out may be the same
+ * buffer.  With pinned buffers the copies overlap the computation: the
+ * host-to-device copy goes in four field groups on a private stream, each
+ * followed by the first derivative pass over those fields, and the
+ * device-to-host copy in up to eight slabs of z-planes, each started when the
+ * last algebra pass has written them.  The result is bitwise that of
+ * cosmos_rk4_step.  Errors: COSMOS_EINVAL (NULL buffer, steps < 0),
+ * COSMOS_EALIGN, COSMOS_EWORKSPACE, COSMOS_ECUDA. */
 int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
                        double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 

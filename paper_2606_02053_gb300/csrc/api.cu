@@ -260,11 +260,18 @@ static ConstraintLauncher constraint_launcher(const cosmos_params* p) {
 // Shared body of cosmos_rhs / cosmos_rk4_stage / cosmos_stage_pass.
 // pass_mask bit 0: fluid pre-pass (primitives, face fluxes); bit 1: derivative
 // pass; bit 2: algebra pass + combine.
+// f_lo, f_hi: field range of the derivative pass (f_hi = 0: all fields);
+// k_lo, k_cnt: plane range of the algebra pass (k_cnt = 0: all planes).
 static int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n,
                      double* out, double* acc, double t_stage, double cdt, double bk, double* ws,
-                     const WsLayout& L, cudaStream_t s, int pass_mask = 7) {
+                     const WsLayout& L, cudaStream_t s, int pass_mask = 7, int f_lo = 0, int f_hi = 0,
+                     int k_lo = 0, int k_cnt = 0) {
   StageArgs a;
   memset(&a, 0, sizeof(a));
+  a.f_lo = f_lo;
+  a.f_hi = f_hi;
+  a.k_lo = k_lo;
+  a.k_cnt = k_cnt;
   a.g = make_devgrid(g);
   a.c = make_coef(g, p->ko_sigma);
   a.ap = algebra_params(p, t_stage);
@@ -436,17 +443,97 @@ int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state,
   return run_stage(g, p, MODE_S4, A, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s);
 }
 
+namespace {
+// Copy stream and events of one cosmos_evolve_host call; destroyed on every
+// return path (work still queued on them completes first).
+struct HostPipeline {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[16] = {};
+  ~HostPipeline() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+}  // namespace
+
 int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
                        double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream) {
   int e = validate(g, p);
   if (e) return e;
   if (!host_in || !host_out || !dev_state || steps < 0) return COSMOS_EINVAL;
-  const size_t bytes = cosmos_field_stride(g) * (size_t)cosmos_nfields(p) * sizeof(double);
+  if (!aligned16(dev_state)) return COSMOS_EALIGN;
+  const size_t fs = cosmos_field_stride(g);
+  const int nf = cosmos_nfields(p);
+  const size_t bytes = fs * (size_t)nf * sizeof(double);
   cudaStream_t s = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(dev_state, host_in, bytes, cudaMemcpyHostToDevice, s));
-  for (int n = 0; n < steps; ++n)
-    if ((e = cosmos_rk4_step(g, p, dev_state, t + n * dt, dt, ws, ws_bytes, stream))) return e;
-  CK(cudaMemcpyAsync(host_out, dev_state, bytes, cudaMemcpyDeviceToHost, s));
+  if (steps == 0) {
+    CK(cudaMemcpyAsync(dev_state, host_in, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(host_out, dev_state, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return COSMOS_OK;
+  }
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RK4);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  double* w = (double*)ws;
+  double* A = w + L.stageA;
+  double* B = w + L.stageB;
+  double* acc = w + L.acc;
+  const double dt2 = 0.5 * dt;
+  // The copies run on their own stream: the host-to-device copy in NCH field
+  // groups, each followed on `s` by the first derivative pass over those
+  // fields; the device-to-host copy in NSL slabs of z-planes, each started as
+  // soon as the last algebra pass has written its planes.
+  constexpr int NCH = 4, NSL_MAX = 8;
+  const int nsl = g->nz < NSL_MAX ? g->nz : NSL_MAX;
+  const size_t plane = (size_t)g->ny * (size_t)g->pitch;
+  HostPipeline hp;
+  CK(cudaStreamCreateWithFlags(&hp.cs, cudaStreamNonBlocking));
+  for (int m = 0; m < 1 + NCH + NSL_MAX; ++m) CK(cudaEventCreateWithFlags(&hp.ev[m], cudaEventDisableTiming));
+  CK(cudaEventRecord(hp.ev[0], s));  // earlier work on `s` may still use dev_state
+  CK(cudaStreamWaitEvent(hp.cs, hp.ev[0], 0));
+  int fb[NCH + 1];
+  for (int c = 0; c <= NCH; ++c) fb[c] = c * nf / NCH;
+  for (int c = 0; c < NCH; ++c) {
+    const size_t off = (size_t)fb[c] * fs, n = (size_t)(fb[c + 1] - fb[c]) * fs;
+    if (n) CK(cudaMemcpyAsync(dev_state + off, host_in + off, n * sizeof(double), cudaMemcpyHostToDevice, hp.cs));
+    CK(cudaEventRecord(hp.ev[1 + c], hp.cs));
+  }
+  for (int step = 0; step < steps; ++step) {
+    const double ts = t + step * dt;
+    if (step == 0) {
+      for (int c = 0; c < NCH; ++c) {
+        CK(cudaStreamWaitEvent(s, hp.ev[1 + c], 0));
+        if (fb[c + 1] > fb[c] &&
+            (e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s, 2, fb[c], fb[c + 1])))
+          return e;
+      }
+      if ((e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s, 5))) return e;
+    } else if ((e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s))) {
+      return e;
+    }
+    if ((e = run_stage(g, p, MODE_S23, A, dev_state, B, acc, ts + dt2, dt2, 2.0, w, L, s))) return e;
+    if ((e = run_stage(g, p, MODE_S23, B, dev_state, A, acc, ts + dt2, dt, 2.0, w, L, s))) return e;
+    if (step + 1 < steps) {
+      if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s))) return e;
+      continue;
+    }
+    if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s, 3))) return e;
+    for (int sl = 0; sl < nsl; ++sl) {
+      const int k0 = sl * g->nz / nsl, k1 = (sl + 1) * g->nz / nsl;
+      if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s, 4, 0, 0, k0,
+                         k1 - k0)))
+        return e;
+      CK(cudaEventRecord(hp.ev[1 + NCH + sl], s));
+      CK(cudaStreamWaitEvent(hp.cs, hp.ev[1 + NCH + sl], 0));
+      for (int f = 0; f < nf; ++f) {
+        const size_t off = (size_t)f * fs + (size_t)k0 * plane;
+        CK(cudaMemcpyAsync(host_out + off, dev_state + off, (size_t)(k1 - k0) * plane * sizeof(double),
+                           cudaMemcpyDeviceToHost, hp.cs));
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(hp.cs));
   CK(cudaStreamSynchronize(s));
   return COSMOS_OK;
 }

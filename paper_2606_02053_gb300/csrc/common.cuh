@@ -89,6 +89,8 @@ struct StageArgs {
   double* D;                       // derivative-pass output [NDER][pts] (see stage_kernel.cuh)
   double cdt;                      // dt * c_{s+1}, or dt/6 in MODE_S4
   double bk;                       // accumulator weight (2 for stages 2, 3)
+  int f_lo, f_hi;                  // derivative pass: only fields f_lo <= f < f_hi (f_hi = 0: all)
+  int k_lo, k_cnt;                 // algebra pass: only planes k_lo .. k_lo + k_cnt - 1 (k_cnt = 0: all)
 };
 
 // Doubles per point of the derivative-pass buffer: first and second

@@ -265,16 +265,19 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
   double* __restrict__ D = a.D;
   constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
   const bool ko_equal = c.ko[0] == c.ko[1] && c.ko[1] == c.ko[2];  // same for every thread
+  const int f_lo = a.f_lo, f_hi = a.f_hi > 0 ? a.f_hi : (1 << 30);  // field range (uniform)
   if constexpr (S::NST > 1) {
 #pragma unroll 1
-    for (int m2 = 0; m2 < T::ND2; ++m2)
-      stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy + m2 * S::NY, sDz + m2 * S::NZ);
+    for (int m2 = 0; m2 < T::ND2; ++m2) {
+      const int f = T::d2_field(m2);
+      if (f >= f_lo && f < f_hi) stage_dydz(a, a.U + (long)f * fs, i0, j0, k, tid, sDy + m2 * S::NY, sDz + m2 * S::NZ);
+    }
   }
   // fields with first derivatives only: direct D1 and KO
 #pragma unroll 1
   for (int m = 0; m < T::ND1; ++m) {
     const int f = T::d1_field(m);
-    if (T::d2_slot(f) >= 0) continue;
+    if (T::d2_slot(f) >= 0 || f < f_lo || f >= f_hi) continue;
     const double* F = a.U + (long)f * fs;
     if (valid) {
       D[(long)(3 * m + 0) * fs + n.c] = fd1<0>(F, n, c);
@@ -289,12 +292,16 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
     __syncthreads();
     if (valid) {
 #pragma unroll 1
-      for (int m2 = 0; m2 < T::ND2; ++m2) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy + m2 * S::NY, sDz + m2 * S::NZ);
+      for (int m2 = 0; m2 < T::ND2; ++m2) {
+        const int f = T::d2_field(m2);
+        if (f >= f_lo && f < f_hi) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy + m2 * S::NY, sDz + m2 * S::NZ);
+      }
     }
     __syncthreads();  // the staging area is reused by the block's next tile
   } else {
 #pragma unroll 1
     for (int m2 = 0; m2 < T::ND2; ++m2) {
+      if (T::d2_field(m2) < f_lo || T::d2_field(m2) >= f_hi) continue;  // uniform across the block
       stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy, sDz);
       __syncthreads();
       if (valid) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy, sDz);
@@ -385,7 +392,7 @@ template <class T, int MODE>
 __global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS) stage_kernel(const StageArgs a) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
+  const int k = blockIdx.z + a.k_lo;
   if (i >= a.g.nx || j >= a.g.ny) return;
   alg_point<T, MODE>(a, a.ap, i, j, k);
 }
@@ -512,7 +519,8 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
     }                                                                                                           \
   };                                                                                                            \
   cudaError_t launch_stage_##NAME(const StageArgs& a, int mode, cudaStream_t s) {                               \
-    const dim3 grid = point_grid(a.g), block(BX, BY);                                                          \
+    dim3 grid = point_grid(a.g), block(BX, BY);                                                                \
+    if (a.k_cnt > 0) grid.z = a.k_cnt;                                                                          \
     if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);         \
     if (mode < 0) return cudaGetLastError();                                                                    \
     switch (mode & 7) {                                                                                             \

@@ -258,6 +258,34 @@ def test_flrw_zeta_evolution_parity_32(C, O):
     assert field_errors(ev.get(), ref).max() <= STEP_TOL
 
 
+@pytest.mark.parametrize("fluid,scalar,n,pitch", [(0, 0, (37, 13, 11), 40), (1, 1, (20, 12, 5), None)])
+def test_evolve_host_matches_device_steps(C, fluid, scalar, n, pitch):
+    """Host-buffer path (copies overlapped with the passes, field groups in,
+    plane slabs out) against cosmos_rk4_step on the device: bitwise."""
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    h = 1.0 / n[0]
+    p = C.make_params(fluid=fluid, scalar=scalar, H0=2.0 * fluid)
+    g = C.make_grid(n, h, pitch=pitch)
+    ev = Evolution(g, p)
+    ev.set_state(inputs.smooth_state(n, seed=77 + fluid, fluid=fluid, scalar=scalar, scale=0.5))
+    U0 = ev.state.clone()
+    dt = 0.25 * h
+    for steps in (0, 1, 3):
+        for pinned in (True, False):
+            host_in = U0.cpu().pin_memory() if pinned else U0.cpu()
+            host_out = torch.full_like(host_in, float("nan"))
+            if pinned:
+                host_out = host_out.pin_memory()
+            dev = torch.empty_like(U0)
+            C.check(C.cosmos_evolve_host(g, p, host_in, host_out, dev, steps, 0.01, dt, ev.ws_rk4))
+            ev.state.copy_(U0)
+            ev.step(0.01, dt, steps=steps)
+            assert torch.equal(host_out, ev.state.cpu()), (steps, pinned)
+            assert torch.equal(dev, ev.state), (steps, pinned)
+
+
 def test_invalid_arguments_launch_nothing(C):
     from paper_2606_02053_gb300.evolve import Evolution
 
