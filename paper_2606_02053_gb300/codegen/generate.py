@@ -65,7 +65,7 @@ def render() -> dict:
             stats.append((name + "_vjp", op_counts(g, adj)))
             body.append(f"// reverse mode of rhs: ops {dict(sorted(op_counts(g, adj).items()))}")
             body.append(emit_function(g, "rhs_vjp", L["names"] + [f"w{f}" for f in range(L["nf"])], adj,
-                                      ["AlgebraParams"]))
+                                      ["AlgebraParams"], accessors=True))
         if name == "vac":
             # reverse mode of H (first constraint) w.r.t. chi, d chi, dd chi: initial-data adjoint
             hb = g.input("hb")

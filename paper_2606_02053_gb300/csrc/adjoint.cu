@@ -40,6 +40,7 @@ static AdjLayout adj_layout(const cosmos_grid* g, const cosmos_params* p, int op
     L.LAM = take(nf * fs);
     L.Dfw = take((size_t)nder(0) * fs);
   }
+  if (op == COSMOS_OP_VJP) L.Dfw = take((size_t)nder(0) * fs);  // derivative pass of the linearisation point
   if (op == COSMOS_OP_ADJOINT || op == COSMOS_OP_VJP) {
     L.CB = take(nin_of(p) * fs);
     if (p->fluid) {
@@ -95,6 +96,20 @@ static cudaError_t vjp_once(const cosmos_grid* g, const cosmos_params* p, const 
   a.knext = knext;
   a.a_lam = a_lam;
   a.a_v = a_v;
+  // finite differences of U (the forward inputs of the algebra) into D; the
+  // forward stages of an adjoint step have all run before the first vjp_once
+  StageArgs d;
+  memset(&d, 0, sizeof(d));
+  d.g = a.g;
+  d.c = a.c;
+  d.U = U;
+  d.D = ws + L.Dfw;
+  d.skip_ko = 1;
+  a.D = d.D;
+  {
+    const cudaError_t e = p->fluid ? launch_stage_fluid(d, -1, s) : launch_stage_vac(d, -1, s);
+    if (e != cudaSuccess) return e;
+  }
   if (p->fluid) {
     double* vp = ws + L.vprim;
     cudaError_t e = launch_fluid_prim(a.g, U, vp, p->w, s);

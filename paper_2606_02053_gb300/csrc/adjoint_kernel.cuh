@@ -22,6 +22,7 @@ struct VjpArgs {
   const double* __restrict__ U;     // linearisation point
   const double* __restrict__ prim;  // primitives at U (fluid)
   const double* __restrict__ W;     // cotangent of F(U) (state layout)
+  const double* __restrict__ D;     // derivative-pass output at U (KO slots unused)
   double* CB;                       // [NIN][pts] input cotangents (pass 1)
   double* FC;                       // [3][34][pts] face-input cotangents (fluid)
   double* VF;                       // [nf][pts] fluid contributions to v (fluid)
@@ -32,22 +33,44 @@ struct VjpArgs {
   double a_lam, a_v;
 };
 
+// Inputs of the reverse algebra at one point: the forward inputs (state,
+// derivative buffer, fluid density) followed by the cotangents W of the
+// outputs, each read from global memory where the generated code uses it.
+template <class T>
+struct VjpIn {
+  const VjpArgs& a;
+  long fs, c;
+  __device__ __forceinline__ double operator[](int k) const {
+    constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+    if (k < T::NF) return ldg(a.U + (long)k * fs, c);
+    if (k < T::NF + NDER0) return ldg(a.D + (long)(k - T::NF) * fs, c);
+    if (k < T::NIN) return ldg(a.prim, c);
+    return ldg(a.W + (long)(k - T::NIN) * fs, c);
+  }
+};
+
+// Input cotangents, stored to CB as soon as the generated code has each one.
+struct VjpOut {
+  double* CB;
+  long fs, c;
+  struct Slot {
+    double* p;
+    __device__ __forceinline__ void operator=(double v) const { *p = v; }
+  };
+  __device__ __forceinline__ Slot operator[](int m) const { return Slot{CB + (long)m * fs + c}; }
+};
+
 template <class T>
 __global__ void __launch_bounds__(BX* BY, 3) vjp_pass1_kernel(const VjpArgs a) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= a.g.nx || j >= a.g.ny) return;
-  const Nbr n = make_nbr(a.g, i, j, k);
   const long fs = a.g.fstride;
-  double in[T::NIN + T::NF];
-  gather<T>(a.U, a.prim, n, a.c, fs, in);
-#pragma unroll
-  for (int f = 0; f < T::NF; ++f) in[T::NIN + f] = ldg(a.W + (long)f * fs, n.c);
-  double out[T::NIN];
+  const long c = ((long)k * a.g.ny + j) * a.g.pitch + i;
+  const VjpIn<T> in{a, fs, c};
+  VjpOut out{a.CB, fs, c};
   T::rhs_vjp(in, out, a.ap);
-#pragma unroll
-  for (int m = 0; m < T::NIN; ++m) a.CB[(long)m * fs + n.c] = out[m];
 }
 
 // Face-flux reverse: H_d(p) enters F at p (-1/h) and at p + e_d (+1/h).
@@ -158,7 +181,8 @@ __global__ void __launch_bounds__(BX* BY) vjp_cell_kernel(const VjpArgs a) {
   for (int f = 0; f < T::NF; ++f) a.VF[(long)f * fs + n.c] = vf[f];
 }
 
-// Transposed stencils + RK4 reverse-sweep accumulation.
+// Transposed stencils + RK4 reverse-sweep accumulation, one field at a time
+// (each v_f depends on the cotangents of field f only).
 template <class T>
 __global__ void __launch_bounds__(BX* BY, 3) vjp_pass2_kernel(const VjpArgs a) {
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -167,42 +191,34 @@ __global__ void __launch_bounds__(BX* BY, 3) vjp_pass2_kernel(const VjpArgs a) {
   if (i >= a.g.nx || j >= a.g.ny) return;
   const Nbr n = make_nbr(a.g, i, j, k);
   const long fs = a.g.fstride;
-  double v[T::NF];
-#pragma unroll
-  for (int f = 0; f < T::NF; ++f) v[f] = ldg(a.CB + (long)f * fs, n.c);
-#pragma unroll
-  for (int m = 0; m < T::ND1; ++m) {
-    const int f = T::d1_field(m);
-    const double* G = a.CB + (long)(T::NF + 3 * m) * fs;
-    v[f] -= fd1<0>(G, n, a.c) + fd1<1>(G + fs, n, a.c) + fd1<2>(G + 2 * fs, n, a.c);
-  }
-#pragma unroll
-  for (int m = 0; m < T::ND2; ++m) {
-    const int f = T::d2_field(m);
-    const double* G = a.CB + (long)(T::NF + 3 * T::ND1 + 6 * m) * fs;
-    double s = fd2<0>(G, n, a.c, ldg(G, n.c));
-    s += fdmix<0, 1>(G + fs, n, a.c.mix[0]);
-    s += fdmix<0, 2>(G + 2 * fs, n, a.c.mix[1]);
-    s += fd2<1>(G + 3 * fs, n, a.c, ldg(G + 3 * fs, n.c));
-    s += fdmix<1, 2>(G + 4 * fs, n, a.c.mix[2]);
-    s += fd2<2>(G + 5 * fs, n, a.c, ldg(G + 5 * fs, n.c));
-    v[f] += s;
-  }
-#pragma unroll
+  const bool ko_equal = a.c.ko[0] == a.c.ko[1] && a.c.ko[1] == a.c.ko[2];
+#pragma unroll 1
   for (int f = 0; f < T::NF; ++f) {
-    if (T::FLUID && f >= 24 && f < 28) continue;
-    const double* Wf = a.W + (long)f * fs;
-    v[f] = ko_add(Wf, n, a.c, ldg(Wf, n.c), v[f]);
-  }
-  if constexpr (T::FLUID) {
-#pragma unroll
-    for (int f = 0; f < T::NF; ++f) v[f] += ldg(a.VF + (long)f * fs, n.c);
-  }
-#pragma unroll
-  for (int f = 0; f < T::NF; ++f) {
+    double v = ldg(a.CB + (long)f * fs, n.c);
+    const int m = T::d1_slot(f);
+    if (m >= 0) {
+      const double* G = a.CB + (long)(T::NF + 3 * m) * fs;
+      v -= fd1<0>(G, n, a.c) + fd1<1>(G + fs, n, a.c) + fd1<2>(G + 2 * fs, n, a.c);
+    }
+    const int m2 = T::d2_slot(f);
+    if (m2 >= 0) {
+      const double* G = a.CB + (long)(T::NF + 3 * T::ND1 + 6 * m2) * fs;
+      double s = fd2<0>(G, n, a.c, ldg(G, n.c));
+      s += fdmix<0, 1>(G + fs, n, a.c.mix[0]);
+      s += fdmix<0, 2>(G + 2 * fs, n, a.c.mix[1]);
+      s += fd2<1>(G + 3 * fs, n, a.c, ldg(G + 3 * fs, n.c));
+      s += fdmix<1, 2>(G + 4 * fs, n, a.c.mix[2]);
+      s += fd2<2>(G + 5 * fs, n, a.c, ldg(G + 5 * fs, n.c));
+      v += s;
+    }
+    if (!(T::FLUID && f >= 24 && f < 28)) {  // KO is symmetric: KO^T w = KO w
+      const double* Wf = a.W + (long)f * fs;
+      v = ko_equal ? v + ko_uniform(Wf, n, a.c, ldg(Wf, n.c)) : ko_add(Wf, n, a.c, ldg(Wf, n.c), v);
+    }
+    if constexpr (T::FLUID) v += ldg(a.VF + (long)f * fs, n.c);
     const long o = (long)f * fs + n.c;
-    a.lam[o] += v[f];
-    if (a.knext) a.knext[o] = a.a_lam * ldg(a.lam0, o) + a.a_v * v[f];
+    a.lam[o] += v;
+    if (a.knext) a.knext[o] = a.a_lam * ldg(a.lam0, o) + a.a_v * v;
   }
 }
 
@@ -221,7 +237,10 @@ struct T_vac_adj {
     static constexpr bool FLUID = IS_FLUID, SCALAR = false;                                                     \
     __device__ static constexpr int d1_field(int m) { return alg_##NAME::d1_field(m); }                        \
     __device__ static constexpr int d2_field(int m) { return alg_##NAME::d2_field(m); }                        \
-    __device__ static __forceinline__ void rhs_vjp(const double* in, double* out, const AlgebraParams& p) {      \
+    __device__ static constexpr int d1_slot(int f) { return alg_##NAME::d1_slot(f); }                          \
+    __device__ static constexpr int d2_slot(int f) { return alg_##NAME::d2_slot(f); }                          \
+    template <class In, class Out>                                                                              \
+    __device__ static __forceinline__ void rhs_vjp(const In& in, Out&& out, const AlgebraParams& p) {           \
       alg_##NAME::rhs_vjp(in, out, p);                                                                          \
     }                                                                                                           \
   };                                                                                                            \

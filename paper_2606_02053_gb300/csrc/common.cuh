@@ -17,6 +17,10 @@ constexpr int BY = 4;   // rows per block
 #define COSMOS_DERIV_ROWS 8
 #endif
 constexpr int DBY = COSMOS_DERIV_ROWS;  // rows per block of the derivative pass
+#ifndef COSMOS_DERIV_PLANES
+#define COSMOS_DERIV_PLANES 1
+#endif
+constexpr int DBZ = COSMOS_DERIV_PLANES;  // z-planes per block of the derivative pass
 
 // Grid description as the kernels see it.
 struct DevGrid {
@@ -91,6 +95,7 @@ struct StageArgs {
   double bk;                       // accumulator weight (2 for stages 2, 3)
   int f_lo, f_hi;                  // derivative pass: only fields f_lo <= f < f_hi (f_hi = 0: all)
   int k_lo, k_cnt;                 // algebra pass: only planes k_lo .. k_lo + k_cnt - 1 (k_cnt = 0: all)
+  int skip_ko;                     // derivative pass: leave the Kreiss-Oliger slots of D unwritten
 };
 
 // Doubles per point of the derivative-pass buffer: first and second
@@ -151,6 +156,8 @@ cudaError_t launch_fluid_flux(const DevGrid& g, const double* U, const double* p
                               int nf_offset_fluid, cudaStream_t s);
 
 inline dim3 point_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
-inline dim3 deriv_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, g.nz); }
+inline dim3 deriv_grid(const DevGrid& g) {
+  return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, (g.nz + DBZ - 1) / DBZ);
+}
 
 }  // namespace cosmos

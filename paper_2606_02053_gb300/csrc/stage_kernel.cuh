@@ -223,12 +223,12 @@ __device__ __forceinline__ void deriv_d2_point(const StageArgs& a, int m2, const
 #pragma unroll
   for (int d = 0; d < 3; ++d) d2[d] = s1[d] * c.d2a[d] - s2[d] * c.d2b[d];
   // KO bracket per axis: (q3 - 2 f0) - 6 s2 + 15 s1, exactly zero for constants
-  double ko;
-  if (ko_equal) {
+  double ko = 0.0;
+  if (a.skip_ko) {
+  } else if (ko_equal) {
     const double Q3 = ((q3[0] + q3[1]) + q3[2]) - __dmul_rn(6.0, f0);
     ko = c.ko[0] * fma(15.0, (s1[0] + s1[1]) + s1[2], fma(-6.0, (s2[0] + s2[1]) + s2[2], Q3));
   } else {
-    ko = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) ko = fma(c.ko[d], fma(15.0, s1[d], fma(-6.0, s2[d], q3[d] - 2.0 * f0)), ko);
   }
@@ -248,17 +248,21 @@ __device__ __forceinline__ void deriv_d2_point(const StageArgs& a, int m2, const
   D[b + 3 * fs] = d2[1];
   D[b + 4 * fs] = dyz;
   D[b + 5 * fs] = d2[2];
-  D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko;
+  if (!a.skip_ko) D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko;
 }
 
-// One BX x DBY tile of z-plane k (block of BX x DBY threads).
+// One BX x DBY tile of the DBZ z-planes k0 .. k0 + DBZ - 1 (block of
+// BX x DBY x DBZ threads; each plane stages into its own shared-memory slice).
 template <class T>
-__device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, int k, double* __restrict__ sDy,
+__device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, int k0, double* __restrict__ sDy,
                                            double* __restrict__ sDz) {
   using S = DerivSmem<T>;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool valid = i < a.g.nx && j < a.g.ny;
+  const int i = i0 + tx, j = j0 + ty, k = k0 + (int)threadIdx.z;
+  const bool plane_ok = k < a.g.nz;  // same for the whole slice
+  const bool valid = i < a.g.nx && j < a.g.ny && plane_ok;
+  sDy += threadIdx.z * (S::NST * S::NY);
+  sDz += threadIdx.z * (S::NST * S::NZ);
   const Nbr n = make_nbr(a.g, i, j, k);
   const long fs = a.g.fstride;
   const Coef& c = a.c;
@@ -270,7 +274,8 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
 #pragma unroll 1
     for (int m2 = 0; m2 < T::ND2; ++m2) {
       const int f = T::d2_field(m2);
-      if (f >= f_lo && f < f_hi) stage_dydz(a, a.U + (long)f * fs, i0, j0, k, tid, sDy + m2 * S::NY, sDz + m2 * S::NZ);
+      if (f >= f_lo && f < f_hi && plane_ok)
+        stage_dydz(a, a.U + (long)f * fs, i0, j0, k, tid, sDy + m2 * S::NY, sDz + m2 * S::NZ);
     }
   }
   // fields with first derivatives only: direct D1 and KO
@@ -283,8 +288,9 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
       D[(long)(3 * m + 0) * fs + n.c] = fd1<0>(F, n, c);
       D[(long)(3 * m + 1) * fs + n.c] = fd1<1>(F, n, c);
       D[(long)(3 * m + 2) * fs + n.c] = fd1<2>(F, n, c);
-      D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] =
-          ko_equal ? ko_uniform(F, n, c, ldg(F, n.c)) : ko_add(F, n, c, ldg(F, n.c), 0.0);
+      if (!a.skip_ko)
+        D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] =
+            ko_equal ? ko_uniform(F, n, c, ldg(F, n.c)) : ko_add(F, n, c, ldg(F, n.c), 0.0);
     }
   }
   // fields with second derivatives
@@ -302,7 +308,7 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
 #pragma unroll 1
     for (int m2 = 0; m2 < T::ND2; ++m2) {
       if (T::d2_field(m2) < f_lo || T::d2_field(m2) >= f_hi) continue;  // uniform across the block
-      stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy, sDz);
+      if (plane_ok) stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy, sDz);
       __syncthreads();
       if (valid) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy, sDz);
       __syncthreads();
@@ -311,9 +317,9 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
 }
 
 template <class T>
-__global__ void __launch_bounds__(BX* DBY, COSMOS_DERIV_MIN_BLOCKS) deriv_kernel(const StageArgs a) {
-  __shared__ double sDy[DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DerivSmem<T>::NST * DerivSmem<T>::NZ];
-  deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
+__global__ void __launch_bounds__(BX* DBY* DBZ, COSMOS_DERIV_MIN_BLOCKS) deriv_kernel(const StageArgs a) {
+  __shared__ double sDy[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NZ];
+  deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z * DBZ, sDy, sDz);
 }
 
 // Inputs of the algebra pass at one point, read from global memory where the
@@ -420,12 +426,12 @@ __device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g
 
 // Persistent batched derivative pass over 32 x 4 tiles of every instance.
 template <class T>
-__global__ void __launch_bounds__(BX* DBY, COSMOS_DERIV_MIN_BLOCKS) batch_deriv_kernel(const StageArgs* __restrict__ args,
-                                                              const BatchTile* __restrict__ tiles, long ntiles) {
-  __shared__ double sDy[DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DerivSmem<T>::NST * DerivSmem<T>::NZ];
+__global__ void __launch_bounds__(BX* DBY* DBZ, COSMOS_DERIV_MIN_BLOCKS)
+    batch_deriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
+  __shared__ double sDy[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NZ];
   for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
     const BatchTile t = tiles[w];
-    deriv_tile<T>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);
+    deriv_tile<T>(args[t.inst], t.a * BX, t.b * DBY, t.c * DBZ, sDy, sDz);
   }
 }
 
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   cudaError_t launch_stage_##NAME(const StageArgs& a, int mode, cudaStream_t s) {                               \
     dim3 grid = point_grid(a.g), block(BX, BY);                                                                \
     if (a.k_cnt > 0) grid.z = a.k_cnt;                                                                          \
-    if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);         \
+    if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY, DBZ), 0, s>>>(a);    \
     if (mode < 0) return cudaGetLastError();                                                                    \
     switch (mode & 7) {                                                                                             \
       case MODE_RHS: stage_kernel<T_##NAME, MODE_RHS><<<grid, block, 0, s>>>(a); break;                        \
@@ -534,7 +540,7 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   cudaError_t launch_batch_stage_##NAME(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping,  \
                                         const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s,      \
                                         const BatchTile* dtiles, long ndtiles) {                                  \
-    batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);                         \
+    batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY, DBZ), 0, s>>>(args, dtiles, ndtiles);                    \
     switch (mode) {                                                                                             \
       case MODE_S1:                                                                                             \
         batch_stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \
