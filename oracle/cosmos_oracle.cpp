@@ -984,6 +984,13 @@ void rk4_step(const Grid& g, const Params& P, double* state, double t, double dt
 /*          beta = B = 0, fluid at rest, E fixed by the discrete Hamiltonian */
 /*          constraint;  zeta = mu exp(-r_e^2/(2 sigma^2)),                  */
 /*          r_e^2 = sum_i ((x_i - c_i)/q_i)^2.                               */
+/*  kind 2: kind 1 plus a massless-scalar isocurvature profile (section     */
+/*          "Examples", spherically symmetric iso-curvature): the scalar    */
+/*          is not part of the background metric; at leading gradient      */
+/*          order phi = Upsilon(x) = A exp(-r_e^2/(2 sigma^2)), Pi = 0, and  */
+/*          the fluid E takes the rest of the discrete Hamiltonian          */
+/*          constraint: E = (R + 2/3 K^2 - At.At)/(16 pi) - rho_phi with    */
+/*          rho_phi = 1/2 chi gt^ij d_i phi d_j phi (fluid and scalar on).  */
 /* id[] = {kind, A, mu, sigma, q0, q1, q2, c0, c1, c2, a0, t}               */
 /* ------------------------------------------------------------------------ */
 void init_all(const Grid& g, const Params& P, const double* id, double* state) {
@@ -1030,10 +1037,11 @@ void init_all(const Grid& g, const Params& P, const double* id, double* state) {
           v[GT + 0] = v[GT + 3] = v[GT + 5] = 1.0;
           v[TRK] = -3.0 * P.H0;
           v[ALP] = 1.0;
+          if (kind == 2) state[(long)P.isc() * N + idx] = id[1] * std::exp(-r2 / (2.0 * sig * sig));  // phi
         }
         for (int f = 0; f < NBSSN; ++f) state[f * N + idx] = v[f];
       }
-  if (kind == 1 && P.fluid) {
+  if ((kind == 1 || kind == 2) && P.fluid) {
     // E from the discrete Hamiltonian constraint with the fluid at rest
     std::vector<double> E(N);
     Params Pv = P;
@@ -1049,7 +1057,15 @@ void init_all(const Grid& g, const Params& P, const double* id, double* state) {
           gather<double>(F, Pv, p, L);
           Geom<double> G;
           geometry<double>(L, G);
-          E[(k * g.n[1] + j) * g.n[0] + i] = (G.Rs + 2.0 / 3.0 * L.K * L.K - G.AA) / (16.0 * PI);
+          double e = (G.Rs + 2.0 / 3.0 * L.K * L.K - G.AA) / (16.0 * PI);
+          if (kind == 2) {
+            double dphi[3], s2 = 0.0;
+            grad<double>(F, P.isc(), p, dphi);
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) s2 = s2 + G.gtu[a][b] * dphi[a] * dphi[b];
+            e = e - 0.5 * L.chi * s2;  // rho of the scalar with Pi = 0
+          }
+          E[(k * g.n[1] + j) * g.n[0] + i] = e;
         }
     int q = P.ifl();
     for (long m = 0; m < N; ++m) {
