@@ -93,7 +93,15 @@ typedef struct {
                         rest with E fixed by the discrete Hamiltonian
                         constraint (requires fluid on);
                         zeta = mu exp(-r_e^2 / (2 sigma^2)),
-                        r_e^2 = sum_i ((x_i - center_i)/q_i)^2 */
+                        r_e^2 = sum_i ((x_i - center_i)/q_i)^2;
+                     2: kind 1 plus a massless-scalar isocurvature profile
+                        (section "Examples", spherically symmetric
+                        iso-curvature; the scalar is not part of the
+                        background metric): phi = Upsilon = A exp(-r_e^2 /
+                        (2 sigma^2)), Pi = 0, and E = (R + 2/3 K^2 -
+                        At.At)/(16 pi) - 1/2 chi gt^ij d_i phi d_j phi, so the
+                        discrete Hamiltonian constraint with both sources
+                        vanishes (requires fluid and scalar on) */
   double A;
   double mu, sigma;
   double q[3];
@@ -112,7 +120,9 @@ size_t cosmos_field_stride(const cosmos_grid* g);
 size_t cosmos_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int op);
 
 /* Initial data (section "Physical system settings", initial-data paragraph).
- * Writes every field of `state`.  ws: COSMOS_OP_INIT bytes. */
+ * Writes every field of `state`.  ws: COSMOS_OP_INIT bytes.  Errors:
+ * COSMOS_EINVAL (unknown kind, gauge wave with fluid, kind 2 without fluid
+ * and scalar, sigma, a0 or q not positive), COSMOS_EALIGN, COSMOS_EWORKSPACE. */
 int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
                      size_t ws_bytes, void* stream);
 

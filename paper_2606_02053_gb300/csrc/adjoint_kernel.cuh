@@ -60,8 +60,12 @@ struct VjpOut {
   __device__ __forceinline__ Slot operator[](int m) const { return Slot{CB + (long)m * fs + c}; }
 };
 
+#ifndef COSMOS_VJP_MIN_BLOCKS
+#define COSMOS_VJP_MIN_BLOCKS 3  // reverse algebra: resident 128-thread blocks per SM the registers are sized for
+#endif
+
 template <class T>
-__global__ void __launch_bounds__(BX* BY, 3) vjp_pass1_kernel(const VjpArgs a) {
+__global__ void __launch_bounds__(BX* BY, COSMOS_VJP_MIN_BLOCKS) vjp_pass1_kernel(const VjpArgs a) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;

@@ -164,6 +164,7 @@ struct InitArgs {
   DevGrid g;
   double x0[3];
   int nf;
+  int isc;  // index of phi (scalar on), else -1
   cosmos_id id;
   double H0;
 };
@@ -205,24 +206,45 @@ __global__ void init_metric_kernel(const InitArgs a, double* __restrict__ U) {
       const double u = (x[d] - a.id.center[d]) / a.id.q[d];
       r2 += u * u;
     }
-    const double zeta = a.id.mu * exp(-r2 / (2.0 * a.id.sigma * a.id.sigma));
+    const double shape = exp(-r2 / (2.0 * a.id.sigma * a.id.sigma));
+    const double zeta = a.id.mu * shape;
     v[0] = exp(-2.0 * zeta) / (a.id.a0 * a.id.a0);
     v[1] = v[4] = v[6] = 1.0;
     v[7] = -3.0 * a.H0;
     v[17] = 1.0;
+    if (a.id.kind == 2) v[a.isc] = a.id.A * shape;  // isocurvature scalar, Pi = 0
   }
   for (int f = 0; f < a.nf; ++f) U[f * fs + c] = v[f];
 }
 
-// tau~ = sqrt(gamma) E with E = (R + 2/3 K^2 - At.At)/(16 pi) = H_vacuum/(16 pi)
-__global__ void init_tau_kernel(const DevGrid g, const double* __restrict__ hm, double* __restrict__ U) {
+// tau~ = sqrt(gamma) E with E = (R + 2/3 K^2 - At.At)/(16 pi) = H_vacuum/(16 pi),
+// less the scalar's energy 1/2 chi gt^ij d_i phi d_j phi when isc >= 0 (Pi = 0;
+// these data have gt = delta, so gt^ij d_i phi d_j phi = |d phi|^2, with the
+// 4th-order centred first derivative of phi).
+__global__ void init_tau_kernel(const DevGrid g, const Coef cf, int isc, const double* __restrict__ hm,
+                                double* __restrict__ U) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
   const long c = ((long)k * g.ny + j) * g.pitch + i;
   const double chi = U[c];
-  const double E = hm[c] / (16.0 * PI);
+  double E = hm[c] / (16.0 * PI);
+  if (isc >= 0) {
+    const Nbr n = make_nbr(g, i, j, k);
+    const double* phi = U + (long)isc * g.fstride;
+    double d2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long o[4] = {d == 0 ? at(n, 1, 0, 0) : d == 1 ? at(n, 0, 1, 0) : at(n, 0, 0, 1),
+                         d == 0 ? at(n, -1, 0, 0) : d == 1 ? at(n, 0, -1, 0) : at(n, 0, 0, -1),
+                         d == 0 ? at(n, 2, 0, 0) : d == 1 ? at(n, 0, 2, 0) : at(n, 0, 0, 2),
+                         d == 0 ? at(n, -2, 0, 0) : d == 1 ? at(n, 0, -2, 0) : at(n, 0, 0, -2)};
+      const double dphi = (phi[o[0]] - phi[o[1]]) * cf.d1a[d] - (phi[o[2]] - phi[o[3]]) * cf.d1b[d];
+      d2 += dphi * dphi;
+    }
+    E -= 0.5 * chi * d2;
+  }
   U[24 * g.fstride + c] = E / (chi * sqrt(chi));
 }
 
@@ -338,19 +360,21 @@ int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_
   if (e) return e;
   if (!id || !state) return COSMOS_EINVAL;
   if (!aligned16(state)) return COSMOS_EALIGN;
-  if (id->kind != 0 && id->kind != 1) return COSMOS_EINVAL;
-  if (id->kind == 0 && p->fluid) return COSMOS_EINVAL;  // the gauge wave is vacuum
-  if (id->kind == 1 && (!(id->sigma > 0.0) || !(id->a0 > 0.0) || !(id->q[0] > 0.0) || !(id->q[1] > 0.0) ||
+  if (id->kind < 0 || id->kind > 2) return COSMOS_EINVAL;
+  if (id->kind == 0 && p->fluid) return COSMOS_EINVAL;                   // the gauge wave is vacuum
+  if (id->kind == 2 && (!p->fluid || !p->scalar)) return COSMOS_EINVAL;  // isocurvature: scalar + fluid
+  if (id->kind >= 1 && (!(id->sigma > 0.0) || !(id->a0 > 0.0) || !(id->q[0] > 0.0) || !(id->q[1] > 0.0) ||
                         !(id->q[2] > 0.0)))
     return COSMOS_EINVAL;
   const WsLayout L = ws_layout(g, p, COSMOS_OP_INIT);
-  const bool need_ws = (id->kind == 1 && p->fluid);
+  const bool need_ws = (id->kind >= 1 && p->fluid);
   if (need_ws && (e = check_ws(L, ws, ws_bytes))) return e;
   cudaStream_t s = (cudaStream_t)stream;
   InitArgs a;
   a.g = make_devgrid(g);
   for (int d = 0; d < 3; ++d) a.x0[d] = g->x0[d];
   a.nf = cosmos_nfields(p);
+  a.isc = p->scalar ? 24 + 4 * p->fluid : -1;
   a.id = *id;
   a.H0 = p->H0;
   init_metric_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a, state);
@@ -369,7 +393,8 @@ int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_
     c.hm = w + L.hm;
     c.partial = w + L.partial;
     CK(launch_constraints_vac(c, s));
-    init_tau_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a.g, w + L.hm, state);
+    init_tau_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a.g, make_coef(g, 0.0), id->kind == 2 ? a.isc : -1,
+                                                             w + L.hm, state);
     CK(cudaGetLastError());
   }
   return COSMOS_OK;

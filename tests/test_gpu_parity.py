@@ -286,6 +286,34 @@ def test_evolve_host_matches_device_steps(C, fluid, scalar, n, pitch):
             assert torch.equal(dev, ev.state), (steps, pinned)
 
 
+def test_isocurvature_init_and_evolution_parity(C, O):
+    """FLRW + zeta + massless-scalar isocurvature data (id kind 2) and 20 RK4
+    steps of the fluid + scalar system against the oracle."""
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = 24
+    h = 1.0 / n
+    x0 = (-(n // 2) * h,) * 3
+    p = C.make_params(fluid=1, scalar=1, w=1.0 / 3.0, H0=40.0)
+    ev = Evolution(C.make_grid(n, h, x0=x0), p)
+    kw = dict(A=0.02, mu=0.3, sigma=0.125, q=(1.0, 0.9, 1.1))
+    ev.init(C.make_id(2, **kw))
+    og = O.OGrid((n, n, n), h, x0=x0)
+    op = oracle_params(O, p)
+    ref = O.init(og, op, O.id_array(2, **kw))
+    assert field_errors(ev.get(), ref).max() <= 1e-12
+    hm, _ = ev.constraints(want_fields=True)
+    assert np.abs(hm[0]).max() <= 1e-12 * 6.0 * 40.0 ** 2
+    assert np.abs(hm[1:]).max() == 0.0
+    dt = 0.25 * h
+    ev.step(0.0, dt, steps=20)
+    O.evolve(og, op, ref, 0.0, dt, 20)
+    assert field_errors(ev.get(), ref).max() <= STEP_TOL
+    pv = C.make_params(fluid=1, scalar=0, H0=40.0)
+    evv = Evolution(C.make_grid(n, h, x0=x0), pv)
+    assert C.cosmos_init_grid(evv.g, pv, C.make_id(2, **kw), evv.state, evv.ws_init) == C.COSMOS_EINVAL
+
+
 def test_invalid_arguments_launch_nothing(C):
     from paper_2606_02053_gb300.evolve import Evolution
 
