@@ -386,7 +386,7 @@ def adjoint_workload(args):
     worst_comp = max(rel(c["fd_compaction"], c["adj_compaction"]) for c in checks)
     t_adj = t_fwd + t_bmin + t_bcomp
     nscal = n ** 3
-    line = {"metric": "adjoint gradient of collapse diagnostics (96^3, 256 steps): speedup over finite differences",
+    line = {"metric": f"adjoint gradient of collapse diagnostics ({n}^3, {steps} steps): speedup over finite differences",
             "value": (2 * nscal * t_fwd) / t_adj, "unit": "x (FD loop time / adjoint time, all zeta points)",
             "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
