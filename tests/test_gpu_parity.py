@@ -314,6 +314,44 @@ def test_isocurvature_init_and_evolution_parity(C, O):
     assert C.cosmos_init_grid(evv.g, pv, C.make_id(2, **kw), evv.state, evv.ws_init) == C.COSMOS_EINVAL
 
 
+def test_single_mode_on_gpu_follows_linear_theory(C, O):
+    """The single-mode FLRW perturbation of test_oracle_linear_mode on the GPU
+    (N = 64 line): mode amplitudes equal the oracle's to 1e-6 of the mode and
+    follow linear theory as the oracle does."""
+    import test_oracle_linear_mode as LM
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = 64
+    h = 1.0 / n
+    p = C.make_params(slicing=1, shift=0, ko_sigma=0.0, fluid=1, w=LM.W, H0=LM.H0)
+    ev = Evolution(C.make_grid((n, 1, 1), h), p)
+    s = np.zeros((28, 1, 1, n))
+    x = h * np.arange(n)
+    s[0] = 1.0
+    s[1] = s[4] = s[6] = 1.0
+    s[7] = -3.0 * LM.H0
+    s[17] = 1.0 + LM.EPS * np.cos(2.0 * np.pi * x)
+    s[24] = 3.0 * LM.H0 ** 2 / (8.0 * np.pi)
+    ev.set_state(s)
+    phase = np.exp(-2j * np.pi * x) * (2.0 / n)
+    dt = 0.25 * h
+    steps = int(round(LM.T_END / dt))
+    times, amps = [0.0], [[s[f, 0, 0] @ phase for _, f, _, _ in LM.COMPARED]]
+    for m in range(steps):
+        ev.step(m * dt, dt)
+        if (m + 1) % 8 == 0:
+            g = ev.get()
+            times.append((m + 1) * dt)
+            amps.append([g[f, 0, 0] @ phase for _, f, _, _ in LM.COMPARED])
+    t, amps = np.array(times), np.array(amps).T
+    t_o, amps_o = LM.oracle_modes(O, n, 8)
+    assert np.array_equal(t, t_o)
+    for (name, _, _, _), a, b in zip(LM.COMPARED, amps, amps_o):
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), name
+    errs = LM.mode_errors(t, amps, 2.0 * np.pi)
+    assert max(errs.values()) < 5e-3, errs
+
+
 def test_invalid_arguments_launch_nothing(C):
     from paper_2606_02053_gb300.evolve import Evolution
 
