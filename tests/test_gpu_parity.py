@@ -366,3 +366,59 @@ def test_invalid_arguments_launch_nothing(C):
     assert C.cosmos_rhs(g, pf, evf.state, torch.empty_like(evf.state), 0.0, small) == C.COSMOS_EWORKSPACE
     assert C.cosmos_rk4_stage(g, p, 5, ev.state, ev.state, out, out, 0.0, 0.1) == C.COSMOS_EINVAL
     assert C.cosmos_init_grid(g, pf, C.make_id(0, A=0.01), evf.state, evf.ws_init) == C.COSMOS_EINVAL
+
+
+@pytest.mark.parametrize("fluid", [0, 1])
+def test_runs_are_deterministic_and_stream_independent(C, fluid):
+    """Two runs from the same state give bitwise the same result, on the
+    default stream and on a side stream (no atomics, fixed reduction order)."""
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = (40, 24, 20)
+    h = 1.0 / 40
+    p = C.make_params(fluid=fluid, H0=2.0 * fluid)
+    ev = Evolution(C.make_grid(n, h), p)
+    s0 = inputs.smooth_state(n, seed=123 + fluid, fluid=fluid, scale=0.5)
+    outs, norms = [], []
+    side = torch.cuda.Stream()
+    for stream in (None, side, None):
+        ev.set_state(s0)
+        torch.cuda.synchronize()  # the state copy (default stream) lands before the side stream starts
+        with torch.cuda.stream(side if stream is side else torch.cuda.current_stream()):
+            for m in range(3):
+                C.check(C.cosmos_rk4_step(ev.g, p, ev.state, m * 0.25 * h, 0.25 * h, ev.ws_rk4,
+                                          torch.cuda.current_stream()))
+            norms.append(ev.constraints()[1])
+        torch.cuda.synchronize()
+        outs.append(ev.state.clone())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    assert np.array_equal(norms[0], norms[1]) and np.array_equal(norms[0], norms[2])
+
+
+def test_rk4_steps_capture_into_a_cuda_graph(C):
+    """cosmos_rk4_step launches only kernels on the given stream (no
+    allocation, no synchronisation), so a sequence of steps can be captured
+    into a CUDA graph; replaying it equals calling the steps directly."""
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n, h = 32, 1.0 / 32
+    p = C.make_params(slicing=0, shift=1)
+    ev = Evolution(C.make_grid(n, h), p)
+    ev.init(C.make_id(0, A=0.01))
+    U0 = ev.state.clone()
+    dt = 0.25 * h
+    ev.step(0.0, dt, steps=5)
+    direct = ev.state.clone()
+    ev.state.copy_(U0)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=s):
+        for m in range(5):
+            C.check(C.cosmos_rk4_step(ev.g, p, ev.state, m * dt, dt, ev.ws_rk4, s))
+    ev.state.copy_(U0)
+    torch.cuda.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(ev.state, direct)
