@@ -187,8 +187,10 @@ int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const doubl
 
 /* ------------------------------------------------------------------------
  * Reverse mode (adjoint) of the evolution, for gradients of collapse
- * diagnostics with respect to the initial curvature perturbation.  Covers the
- * BSSN + fluid system (scalar off); every reverse step is the exact transpose
+ * diagnostics with respect to the initial curvature perturbation.  Covers
+ * every matter variant (vacuum, fluid, scalar, fluid + scalar); the initial-
+ * data maps and the compaction function need the fluid on.  Every reverse
+ * step is the exact transpose
  * of the corresponding discrete forward step (minmod, max and |.| take the
  * derivative of the branch taken).
  * ------------------------------------------------------------------------ */

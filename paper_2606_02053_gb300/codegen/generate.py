@@ -12,7 +12,7 @@ from . import bssn
 from . import fluid as fluid_dsl
 from .expr import Ex, emit_function, op_counts, vjp
 
-ADJOINT_VARIANTS = ("vac", "fluid")
+ADJOINT_VARIANTS = ("vac", "fluid", "scalar", "fluid_scalar")
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(os.path.dirname(HERE), "csrc", "generated")

@@ -18,11 +18,25 @@ struct AdjLayout {
   size_t U2, U3, U4, KB, KB2, LAM, Dfw, CB, prim, flux, vprim, FC, VF, CB10, total_bytes;
 };
 
-static int nin_of(const cosmos_params* p) { return p->fluid ? alg_fluid::NIN : alg_vac::NIN; }
+static int nin_of(const cosmos_params* p) {
+  if (p->fluid) return p->scalar ? alg_fluid_scalar::NIN : alg_fluid::NIN;
+  return p->scalar ? alg_scalar::NIN : alg_vac::NIN;
+}
+
+// Forward stage and reverse launchers of the matter variant.
+static cudaError_t launch_stage_for(const cosmos_params* p, const StageArgs& a, int mode, cudaStream_t s) {
+  if (p->fluid) return p->scalar ? launch_stage_fluid_scalar(a, mode, s) : launch_stage_fluid(a, mode, s);
+  return p->scalar ? launch_stage_scalar(a, mode, s) : launch_stage_vac(a, mode, s);
+}
+
+static cudaError_t launch_vjp_for(const cosmos_params* p, const VjpArgs& a, cudaStream_t s) {
+  if (p->fluid) return p->scalar ? launch_vjp_fluid_scalar(a, s) : launch_vjp_fluid(a, s);
+  return p->scalar ? launch_vjp_scalar(a, s) : launch_vjp_vac(a, s);
+}
 
 static AdjLayout adj_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
   const size_t fs = (size_t)g->pitch * g->ny * g->nz;
-  const int nf = 24 + 4 * p->fluid;
+  const int nf = 24 + 4 * p->fluid + 2 * p->scalar;
   AdjLayout L;
   memset(&L, 0, sizeof(L));
   size_t off = 0;
@@ -38,9 +52,9 @@ static AdjLayout adj_layout(const cosmos_grid* g, const cosmos_params* p, int op
     L.KB = take(nf * fs);
     L.KB2 = take(nf * fs);
     L.LAM = take(nf * fs);
-    L.Dfw = take((size_t)nder(0) * fs);
+    L.Dfw = take((size_t)nder(p->scalar) * fs);
   }
-  if (op == COSMOS_OP_VJP) L.Dfw = take((size_t)nder(0) * fs);  // derivative pass of the linearisation point
+  if (op == COSMOS_OP_VJP) L.Dfw = take((size_t)nder(p->scalar) * fs);  // derivative pass of the linearisation point
   if (op == COSMOS_OP_ADJOINT || op == COSMOS_OP_VJP) {
     L.CB = take(nin_of(p) * fs);
     if (p->fluid) {
@@ -59,7 +73,6 @@ static AdjLayout adj_layout(const cosmos_grid* g, const cosmos_params* p, int op
 static int check_adj(const cosmos_grid* g, const cosmos_params* p) {
   const int e = validate(g, p);
   if (e) return e;
-  if (p->scalar) return COSMOS_EINVAL;  // reverse mode covers the BSSN + fluid system
   return COSMOS_OK;
 }
 
@@ -107,7 +120,7 @@ static cudaError_t vjp_once(const cosmos_grid* g, const cosmos_params* p, const 
   d.skip_ko = 1;
   a.D = d.D;
   {
-    const cudaError_t e = p->fluid ? launch_stage_fluid(d, -1, s) : launch_stage_vac(d, -1, s);
+    const cudaError_t e = launch_stage_for(p, d, -1, s);
     if (e != cudaSuccess) return e;
   }
   if (p->fluid) {
@@ -117,9 +130,8 @@ static cudaError_t vjp_once(const cosmos_grid* g, const cosmos_params* p, const 
     a.prim = vp;
     a.FC = ws + L.FC;
     a.VF = ws + L.VF;
-    return launch_vjp_fluid(a, s);
   }
-  return launch_vjp_vac(a, s);
+  return launch_vjp_for(p, a, s);
 }
 
 __global__ void scale_copy(const double* __restrict__ x, double a, double* __restrict__ y, long n) {
@@ -155,9 +167,8 @@ static cudaError_t fwd_stage(const cosmos_grid* g, const cosmos_params* p, const
     if ((e = launch_fluid_flux(a.g, U_s, ws + L.prim, ws + L.flux, p->w, 24, s)) != cudaSuccess) return e;
     a.prim = ws + L.prim;
     a.flux = ws + L.flux;
-    return launch_stage_fluid(a, MODE_S1, s);
   }
-  return launch_stage_vac(a, MODE_S1, s);
+  return launch_stage_for(p, a, MODE_S1, s);
 }
 
 // Compaction: per-block partial histograms over shells k = floor(sqrt(m)) + 1,

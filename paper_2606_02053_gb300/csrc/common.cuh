@@ -147,6 +147,8 @@ cudaError_t launch_constraints_fluid_scalar(const ConstraintArgs& a, cudaStream_
 struct VjpArgs;
 cudaError_t launch_vjp_vac(const VjpArgs& a, cudaStream_t s);
 cudaError_t launch_vjp_fluid(const VjpArgs& a, cudaStream_t s);
+cudaError_t launch_vjp_scalar(const VjpArgs& a, cudaStream_t s);
+cudaError_t launch_vjp_fluid_scalar(const VjpArgs& a, cudaStream_t s);
 cudaError_t launch_init_zeta_vjp(const DevGrid& g, const Coef& c, const AlgebraParams& ap, const double* U,
                                  const double* lam, double* CB10, int fluid, double* zbar, cudaStream_t s);
 

@@ -36,37 +36,41 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda().reshape(-1)
 
 
-@pytest.mark.parametrize("fluid", [0, 1])
-def test_rhs_vjp_matches_oracle_tape(C, O, fluid):
+MATTER = [(0, 0), (1, 0), (0, 1), (1, 1)]  # (fluid, scalar)
+
+
+@pytest.mark.parametrize("fluid,scalar", MATTER)
+def test_rhs_vjp_matches_oracle_tape(C, O, fluid, scalar):
     from paper_2606_02053_gb300 import inputs
 
     n = (9, 8, 7)
     h = 1.0 / 9
-    p = C.make_params(slicing=0, shift=1, eta=1.3, ko_sigma=0.2, fluid=fluid, H0=2.0 * fluid)
+    kw = dict(slicing=0, shift=1, eta=1.3, ko_sigma=0.2, fluid=fluid, scalar=scalar, H0=2.0 * fluid)
+    p = C.make_params(**kw)
     g = C.make_grid(n, h)
-    U = inputs.smooth_state(n, seed=60 + fluid, fluid=fluid, scale=0.5)
+    U = inputs.smooth_state(n, seed=60 + fluid + 2 * scalar, fluid=fluid, scalar=scalar, scale=0.5)
     w = np.random.default_rng(7).standard_normal(U.shape)
     v = torch.empty_like(dev(U))
     C.check(C.cosmos_rhs_vjp(g, p, dev(U), dev(w), v, 0.1, ws(C, g, p, C.COSMOS_OP_VJP)))
-    op = O.params_array(slicing=0, shift=1, eta=1.3, ko_sigma=0.2, fluid=fluid, H0=2.0 * fluid)
-    ref = O.rhs_vjp(O.OGrid(n, h), op, U, w, 0.1)
+    ref = O.rhs_vjp(O.OGrid(n, h), O.params_array(**kw), U, w, 0.1)
     assert rel_err(v.cpu().numpy().reshape(U.shape), ref) <= 1e-10
 
 
-@pytest.mark.parametrize("fluid", [0, 1])
-def test_adjoint_step_matches_oracle(C, O, fluid):
+@pytest.mark.parametrize("fluid,scalar", MATTER)
+def test_adjoint_step_matches_oracle(C, O, fluid, scalar):
     from paper_2606_02053_gb300 import inputs
 
     n = (8, 7, 7)
     h = 1.0 / 8
-    p = C.make_params(slicing=0, shift=1, eta=1.0, ko_sigma=0.1, fluid=fluid, H0=2.0 * fluid)
+    kw = dict(slicing=0, shift=1, eta=1.0, ko_sigma=0.1, fluid=fluid, scalar=scalar, H0=2.0 * fluid)
+    p = C.make_params(**kw)
     g = C.make_grid(n, h)
-    U = inputs.smooth_state(n, seed=70 + fluid, fluid=fluid, scale=0.5)
+    U = inputs.smooth_state(n, seed=70 + fluid + 2 * scalar, fluid=fluid, scalar=scalar, scale=0.5)
     lam = np.random.default_rng(8).standard_normal(U.shape)
     out = torch.empty_like(dev(U))
     dt = 0.25 * h
     C.check(C.cosmos_adjoint_step(g, p, dev(U), dev(lam), out, 0.05, dt, ws(C, g, p, C.COSMOS_OP_ADJOINT)))
-    op = O.params_array(slicing=0, shift=1, eta=1.0, ko_sigma=0.1, fluid=fluid, H0=2.0 * fluid)
+    op = O.params_array(**kw)
     ref = O.adjoint_step(O.OGrid(n, h), op, U, lam, 0.05, dt)
     assert rel_err(out.cpu().numpy().reshape(U.shape), ref) <= 1e-10
     # in place (lam_n = lam_np1) gives the same result
