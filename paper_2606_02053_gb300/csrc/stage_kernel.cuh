@@ -1,12 +1,16 @@
-// Fused BSSN right-hand side + RK4 stage kernel (one grid point per thread).
+// BSSN right-hand side + RK4 stage, as two passes per stage (FP64 throughout):
 //
-// Per point: 4th-order centred first and second derivatives of every field
-// the algebra needs (loaded straight from global memory through the
-// read-only cache -- the sweep is bound by the FP64 pipe, not by memory),
-// the generated pointwise algebra, 6th-derivative Kreiss-Oliger dissipation
-// on the non-fluid fields, the Kurganov-Tadmor flux divergence on the fluid
-// fields, and the RK4 stage combine.  Every stencil is written so that its
-// large cancellations happen in exact neighbour differences.
+//  * derivative pass (deriv_kernel, batch_deriv_kernel): for one BX x DBY tile
+//    of a z-plane, every 4th-order centred first and second derivative the
+//    algebra needs and the 6th-derivative Kreiss-Oliger term of every
+//    non-fluid field, written to the derivative buffer D;
+//  * algebra pass (stage_kernel, batch_stage_kernel): one point per thread,
+//    the generated pointwise BSSN + matter algebra on the state and D, the KO
+//    term or the Kurganov-Tadmor flux divergence, and the RK4 stage combine.
+//
+// Every stencil is written so that its large cancellations happen in exact
+// neighbour differences.  Also here: the constraint kernel and the per-variant
+// launchers (COSMOS_DEFINE_VARIANT).
 #pragma once
 
 #include "common.cuh"
@@ -138,7 +142,7 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
 // ---------------------------------------------------------------------------
 // Stage = derivative pass + algebra pass.
 //
-// Derivative pass (one 32 x 4 tile of one z-plane per block): writes every
+// Derivative pass (one BX x DBY tile of DBZ z-planes per block): writes every
 // finite difference the algebra needs, and the Kreiss-Oliger term of every
 // non-fluid field, into D (layout: D[3 m + d] first derivative d of the m-th
 // first-derivative field, D[3 ND1 + 6 m + p] second derivative p of the m-th
@@ -147,6 +151,8 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
 // once per tile point (with a 2-point halo) into shared memory, and the mixed
 // derivatives are D_x(D_y f), D_x(D_z f), D_y(D_z f) of those values; along x
 // the neighbour differences d_k = f(+-k) - f0 are shared by D1, D2 and KO.
+// Optional restrictions (StageArgs): a field range f_lo .. f_hi, no KO slots
+// (skip_ko, for the reverse mode), and for the algebra pass a plane range.
 // Algebra pass (any point mapping): the generated pointwise algebra on the
 // state values and D, KO and the fluid flux divergence, and the RK4 combine.
 // ---------------------------------------------------------------------------
