@@ -503,9 +503,17 @@ def main():
         for k in range(e2e_steps):
             C.check(C.cosmos_evolve_host(g, p, host_in, host_out, dev, 1, k * dt, dt, ev.ws_rk4, stream))
         rounds.append(nranks * pts * e2e_steps / max_over_ranks(time.perf_counter() - t0))
+    # plain copy rates of the host link in this run (context for the rounds)
+    link = {}
+    for name, (dst, src) in (("h2d_GBps", (dev, host_in)), ("d2h_GBps", (host_out, dev))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        link[name] = nbytes / (time.perf_counter() - t0) / 1e9
     e2e = {"value": statistics.median(rounds), "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "rounds": rounds,
-           "steps_per_round": e2e_steps}
+           "steps_per_round": e2e_steps, "link": link}
 
     # ---- FP64 peak of this GPU (in-run DFMA probe) ----
     scratch = torch.empty(152 * 8 * 256, dtype=torch.float64, device=f"cuda:{local}")

@@ -100,14 +100,26 @@ __device__ __forceinline__ double ko_add(const double* __restrict__ F, const Nbr
 // axes are summed first, P_k = sum_d (f(+k e_d) + f(-k e_d)), and combined once:
 // (P3 - P2) - 5 (P2 - P1) + 10 (P1 - 6 f0).  For a constant field every P_k and
 // 6 f0 are the same single rounding of 6 f0, so each bracket is exactly zero.
-__device__ __forceinline__ double ko_uniform(const double* __restrict__ F, const Nbr& n, const Coef& c, double f0) {
+// ko_bracket returns the bracket; the term is c.ko[0] times it.
+__device__ __forceinline__ double ko_bracket(const double* __restrict__ F, const Nbr& n, double f0) {
   double P[3];
 #pragma unroll
   for (int k = 1; k <= 3; ++k)
     P[k - 1] = ((ldg(F, disp<0>(n, k)) + ldg(F, disp<0>(n, -k))) + (ldg(F, disp<1>(n, k)) + ldg(F, disp<1>(n, -k)))) +
                (ldg(F, disp<2>(n, k)) + ldg(F, disp<2>(n, -k)));
   const double t = P[0] - __dmul_rn(6.0, f0);  // __dmul_rn: the product is rounded, never fused
-  return c.ko[0] * fma(10.0, t, fma(-5.0, P[1] - P[0], P[2] - P[1]));
+  return fma(10.0, t, fma(-5.0, P[1] - P[0], P[2] - P[1]));
+}
+
+__device__ __forceinline__ double ko_uniform(const double* __restrict__ F, const Nbr& n, const Coef& c, double f0) {
+  return c.ko[0] * ko_bracket(F, n, f0);
+}
+
+// Factor the algebra pass applies to the KO slots of D: with equal spacing the
+// derivative pass stores the bracket and the scale c.ko[0] is applied in the
+// algebra pass's fused multiply-add; otherwise the slots hold the full term.
+__device__ __forceinline__ double ko_slot_scale(const Coef& c) {
+  return (c.ko[0] == c.ko[1] && c.ko[1] == c.ko[2]) ? c.ko[0] : 1.0;
 }
 
 // Inputs of the generated algebra at one point (layout documented in codegen/bssn.py).
@@ -146,7 +158,8 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
 // finite difference the algebra needs, and the Kreiss-Oliger term of every
 // non-fluid field, into D (layout: D[3 m + d] first derivative d of the m-th
 // first-derivative field, D[3 ND1 + 6 m + p] second derivative p of the m-th
-// second-derivative field, D[NDER0 + ko_slot(f)] KO term of field f).  For the
+// second-derivative field, D[NDER0 + ko_slot(f)] KO term of field f, divided by
+// c.ko[0] when the spacing is equal -- see ko_slot_scale).  For the
 // second-derivative fields the first derivatives along y and z are computed
 // once per tile point (with a 2-point halo) into shared memory, and the mixed
 // derivatives are D_x(D_y f), D_x(D_z f), D_y(D_z f) of those values; along x
@@ -233,7 +246,7 @@ __device__ __forceinline__ void deriv_d2_point(const StageArgs& a, int m2, const
   if (a.skip_ko) {
   } else if (ko_equal) {
     const double Q3 = ((q3[0] + q3[1]) + q3[2]) - __dmul_rn(6.0, f0);
-    ko = c.ko[0] * fma(15.0, (s1[0] + s1[1]) + s1[2], fma(-6.0, (s2[0] + s2[1]) + s2[2], Q3));
+    ko = fma(15.0, (s1[0] + s1[1]) + s1[2], fma(-6.0, (s2[0] + s2[1]) + s2[2], Q3));  // scaled in the algebra pass
   } else {
 #pragma unroll
     for (int d = 0; d < 3; ++d) ko = fma(c.ko[d], fma(15.0, s1[d], fma(-6.0, s2[d], q3[d] - 2.0 * f0)), ko);
@@ -296,7 +309,7 @@ __device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, i
       D[(long)(3 * m + 2) * fs + n.c] = fd1<2>(F, n, c);
       if (!a.skip_ko)
         D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] =
-            ko_equal ? ko_uniform(F, n, c, ldg(F, n.c)) : ko_add(F, n, c, ldg(F, n.c), 0.0);
+            ko_equal ? ko_bracket(F, n, ldg(F, n.c)) : ko_add(F, n, c, ldg(F, n.c), 0.0);
     }
   }
   // fields with second derivatives
@@ -353,6 +366,7 @@ struct AlgOut {
   const StageArgs& a;
   long fs, c;
   long cm[3];
+  double ko_scale;  // ko_slot_scale(a.c)
   struct Slot {
     const AlgOut& o;
     int f;
@@ -366,7 +380,7 @@ struct AlgOut {
         r -= (ldg(H + 4 * fs, c) - ldg(H + 4 * fs, o.cm[1])) * a.c.ih[1];
         r -= (ldg(H + 8 * fs, c) - ldg(H + 8 * fs, o.cm[2])) * a.c.ih[2];
       } else {
-        r += ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c);
+        r = fma(o.ko_scale, ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c), r);
       }
       const long ofs = (long)f * fs + c;
       if constexpr (MODE == MODE_RHS) {
@@ -391,7 +405,7 @@ __device__ __forceinline__ void alg_point(const StageArgs& a, const AlgebraParam
   const long fs = a.g.fstride;
   const long c = ((long)k * a.g.ny + j) * a.g.pitch + i;
   const AlgIn<T> in{a.U, a.D, a.prim, fs, c};
-  AlgOut<T, MODE> out{a, fs, c, {0, 0, 0}};
+  AlgOut<T, MODE> out{a, fs, c, {0, 0, 0}, ko_slot_scale(a.c)};
   if constexpr (T::FLUID) {
     out.cm[0] = c - i + wrap_index(i - 1, a.g.nx);
     out.cm[1] = c + (long)(wrap_index(j - 1, a.g.ny) - j) * a.g.pitch;
