@@ -36,6 +36,7 @@ Coef make_coef(const cosmos_grid* g, double sigma) {
   c.mix[0] = 1.0 / (144.0 * g->h[0] * g->h[1]);
   c.mix[1] = 1.0 / (144.0 * g->h[0] * g->h[2]);
   c.mix[2] = 1.0 / (144.0 * g->h[1] * g->h[2]);
+  c.ko_s = (c.ko[0] == c.ko[1] && c.ko[1] == c.ko[2]) ? c.ko[0] : 1.0;
   return c;
 }
 

@@ -68,6 +68,8 @@ struct Coef {
   double mix[3];          // mixed xy, xz, yz:  1/(144 h_a h_b)
   double ko[3];           // sigma/(64 h_d)
   double ih[3];           // 1/h_d (flux divergence)
+  double ko_s;            // factor of the KO slots of the derivative buffer: ko[0] with equal
+                          // spacing (the slots hold the bracket), else 1 (they hold the term)
 };
 
 Coef make_coef(const cosmos_grid* g, double sigma);

@@ -115,12 +115,6 @@ __device__ __forceinline__ double ko_uniform(const double* __restrict__ F, const
   return c.ko[0] * ko_bracket(F, n, f0);
 }
 
-// Factor the algebra pass applies to the KO slots of D: with equal spacing the
-// derivative pass stores the bracket and the scale c.ko[0] is applied in the
-// algebra pass's fused multiply-add; otherwise the slots hold the full term.
-__device__ __forceinline__ double ko_slot_scale(const Coef& c) {
-  return (c.ko[0] == c.ko[1] && c.ko[1] == c.ko[2]) ? c.ko[0] : 1.0;
-}
 
 // Inputs of the generated algebra at one point (layout documented in codegen/bssn.py).
 template <class T>
@@ -159,7 +153,7 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
 // non-fluid field, into D (layout: D[3 m + d] first derivative d of the m-th
 // first-derivative field, D[3 ND1 + 6 m + p] second derivative p of the m-th
 // second-derivative field, D[NDER0 + ko_slot(f)] KO term of field f, divided by
-// c.ko[0] when the spacing is equal -- see ko_slot_scale).  For the
+// c.ko[0] when the spacing is equal -- see Coef::ko_s).  For the
 // second-derivative fields the first derivatives along y and z are computed
 // once per tile point (with a 2-point halo) into shared memory, and the mixed
 // derivatives are D_x(D_y f), D_x(D_z f), D_y(D_z f) of those values; along x
@@ -366,7 +360,6 @@ struct AlgOut {
   const StageArgs& a;
   long fs, c;
   long cm[3];
-  double ko_scale;  // ko_slot_scale(a.c)
   struct Slot {
     const AlgOut& o;
     int f;
@@ -380,7 +373,7 @@ struct AlgOut {
         r -= (ldg(H + 4 * fs, c) - ldg(H + 4 * fs, o.cm[1])) * a.c.ih[1];
         r -= (ldg(H + 8 * fs, c) - ldg(H + 8 * fs, o.cm[2])) * a.c.ih[2];
       } else {
-        r = fma(o.ko_scale, ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c), r);
+        r = fma(a.c.ko_s, ldg(a.D + (long)(NDER0 + ko_slot<T>(f)) * fs, c), r);  // see Coef::ko_s
       }
       const long ofs = (long)f * fs + c;
       if constexpr (MODE == MODE_RHS) {
@@ -405,7 +398,7 @@ __device__ __forceinline__ void alg_point(const StageArgs& a, const AlgebraParam
   const long fs = a.g.fstride;
   const long c = ((long)k * a.g.ny + j) * a.g.pitch + i;
   const AlgIn<T> in{a.U, a.D, a.prim, fs, c};
-  AlgOut<T, MODE> out{a, fs, c, {0, 0, 0}, ko_slot_scale(a.c)};
+  AlgOut<T, MODE> out{a, fs, c, {0, 0, 0}};
   if constexpr (T::FLUID) {
     out.cm[0] = c - i + wrap_index(i - 1, a.g.nx);
     out.cm[1] = c + (long)(wrap_index(j - 1, a.g.ny) - j) * a.g.pitch;
