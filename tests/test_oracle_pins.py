@@ -351,3 +351,52 @@ def test_kt_step_boosted_fluid_speed_is_velocity_addition(O, v):
     for f, (Fv, Uv) in enumerate([(FE, E), (FJ, J)]):
         expect = -(0.5 * (Fv[m] - Fv[m - 1]) - 0.5 * a * (Uv[m] - Uv[m - 1])) / h
         assert abs(r[24 + f, 0, 0, m - 1] - expect) <= 1e-12 * abs(expect), (f, r[24 + f, 0, 0, m - 1], expect)
+
+
+# ---------------------------------------------------------------------------
+# Scalar field pins (section "Physical system settings": box phi = 0).
+# ---------------------------------------------------------------------------
+def test_scalar_plane_wave_on_flat_space_4th_order(O):
+    """phi = eps sin(k (x - t)) solves box phi = 0 on flat space; with Pi =
+    -n.d phi = eps k cos(k (x - t)) and eps = 1e-6 the metric response is
+    O(eps^2).  The oracle's phi after one crossing time converges to it at 4th
+    order (centred stencils, RK4 with dt = h/4)."""
+    eps = 1e-6
+    errs = []
+    for n in (16, 32, 64):
+        h = 1.0 / n
+        g = O.OGrid((n, 1, 1), h)
+        P = O.params_array(slicing=1, shift=0, scalar=1, ko_sigma=0.0)
+        s = np.zeros((26, 1, 1, n))
+        x = h * np.arange(n)
+        k = 2 * np.pi
+        s[CHI] = 1.0
+        s[GT] = s[GT + 3] = s[GT + 5] = 1.0
+        s[ALP] = 1.0
+        s[24] = eps * np.sin(k * x)
+        s[25] = eps * k * np.cos(k * x)
+        T = 0.5
+        steps = int(round(T / (0.25 * h)))
+        O.evolve(g, P, s, 0.0, T / steps, steps)
+        errs.append(np.abs(s[24, 0, 0] - eps * np.sin(k * (x - T))).max() / eps)
+    assert errs[2] < 1e-5, errs
+    assert 13 < errs[0] / errs[1] < 19 and 14 < errs[1] / errs[2] < 18, errs
+
+
+def test_homogeneous_scalar_momentum_redshifts_as_a_minus_3(O):
+    """A homogeneous Pi in radiation FLRW obeys d_t Pi = alpha K Pi = -3 H Pi,
+    so Pi a^3 stays constant (a = chi^{-1/2}), and d_t phi = -alpha Pi
+    integrates to phi(T) = -Pi0 (1 - (1 + 2 H0 T)^{-1/2}) / H0; RK4 error O(dt^4)."""
+    H0, T = 1.0, 2.0
+    errs = []
+    for nsteps in (100, 200):
+        g = O.OGrid((1, 1, 1), 1.0)
+        P = O.params_array(slicing=0, shift=1, fluid=1, scalar=1, w=1.0 / 3.0, H0=H0)
+        s = O.init(g, P, O.id_array(1, mu=0.0))
+        s[29] = 1e-4  # Pi (its energy 1/2 Pi^2 is ~1e-9 of the fluid's)
+        O.evolve(g, P, s, 0.0, T / nsteps, nsteps)
+        a = s[CHI, 0, 0, 0] ** -0.5
+        phi_exact = -1e-4 * (1.0 - (1.0 + 2.0 * H0 * T) ** -0.5) / H0
+        errs.append(max(abs(s[29, 0, 0, 0] * a ** 3 / 1e-4 - 1.0), abs(s[28, 0, 0, 0] / phi_exact - 1.0)))
+    assert errs[1] < 1e-7, errs
+    assert 12 < errs[0] / errs[1] < 20, errs
