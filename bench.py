@@ -62,7 +62,8 @@ def kernel_sources_hash():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 20 for the sweep and the reference arm, 150 for the scan)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help=argparse.SUPPRESS)
@@ -74,7 +75,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-grid", type=int, default=96, help=argparse.SUPPRESS)
     ap.add_argument("--instances", type=int, default=64, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 150 if a.workload == "scan" and a.impl != "reference" else 20
+    return a
 
 
 def flrw_workload(args):
@@ -195,11 +199,12 @@ def scan_workload(args):
     value = total_pts * K / t_batch
     if rank != 0:
         return
-    line = {"metric": "batched threshold-scan FP64 grid-point RK4 updates/sec (64 instances, 64^3-96^3)",
+    line = {"metric": f"batched threshold-scan FP64 grid-point RK4 updates/sec ({len(inst_all)} instances, "
+                      f"{min(d['n'] for d in inst_all)}^3-{max(d['n'] for d in inst_all)}^3)",
             "value": value, "unit": UNIT, "steps": K, "warmup": W,
             "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "n_gpus": ws_,
-            "config": {"workload": "flrw_zeta_scan_64_instances_fluid_w1/3", "instances": len(inst_all),
+            "config": {"workload": f"flrw_zeta_scan_{len(inst_all)}_instances_fluid_w1/3", "instances": len(inst_all),
                        "points_total": int(total_pts), "grid_sizes": [d["n"] for d in inst_all]},
             "per_instance_loop_value": total_pts * K / t_loop, "batched_speedup": t_loop / t_batch,
             "batched_vs_loop_max_abs_diff": max_diff, "autotune": tune,
