@@ -17,6 +17,7 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   constraints : autodiff ADM constraints (4th-order convergence), gauge wave.
   init        : gauge-wave closed form; FLRW + zeta gives H = 0 (discrete).
   flop_count  : counts only; no physics.
+  fluid_rho   : round trip (rho, v) -> (E, J) -> rho against the definitions.
   rhs_vjp / adjoint_step : tape reverse mode of rhs / rk4_step; pinned by
       finite-difference dot-product tests against the (pinned) forward map.
 """
@@ -72,6 +73,7 @@ def lib():
         L.oracle_flop_count.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
         L.oracle_rhs_vjp.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D, _D]
         L.oracle_flop_count_parts.argtypes = [_I, _D, _D, _D, _D, ctypes.c_double, _D]
+        L.oracle_fluid_rho.argtypes = [_D, _D, ctypes.c_long, ctypes.c_double, _D]
         _lib = L
     return _lib
 
@@ -235,6 +237,15 @@ def adjoint_step(g: OGrid, params, state, lam, t, dt):
     out += v
     kb = dt / 6.0 * lam + 0.5 * dt * v
     out += rhs_vjp(g, params, U[0], kb, ts[0])
+    return out
+
+
+def fluid_rho(E, J2, w):
+    """Rest-frame density recovered from E and J^2 for P = w rho."""
+    E = np.ascontiguousarray(E, dtype=np.float64).ravel()
+    J2 = np.ascontiguousarray(J2, dtype=np.float64).ravel()
+    out = np.empty_like(E)
+    lib().oracle_fluid_rho(_dp(E), _dp(J2), E.size, float(w), _dp(out))
     return out
 
 

@@ -1086,6 +1086,12 @@ extern "C" {
 
 int oracle_nfields(const double* params) { return unpack_params(params).nf(); }
 
+/* Fluid rest-frame density from E and J^2 = gamma^ij J_i J_j (the recovery
+ * used by the right-hand side), for n values. */
+void oracle_fluid_rho(const double* E, const double* J2, long n, double w, double* rho) {
+  for (long m = 0; m < n; ++m) rho[m] = fluid_rho<double>(E[m], J2[m], w);
+}
+
 void oracle_set_threads(int n) {
 #ifdef _OPENMP
   omp_set_num_threads(n);

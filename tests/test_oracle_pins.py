@@ -400,3 +400,25 @@ def test_homogeneous_scalar_momentum_redshifts_as_a_minus_3(O):
         errs.append(max(abs(s[29, 0, 0, 0] * a ** 3 / 1e-7 - 1.0), abs(s[28, 0, 0, 0] / phi_exact - 1.0)))
     assert errs[1] < 1e-7, errs
     assert 12 < errs[0] / errs[1] < 20, errs
+
+
+# ---------------------------------------------------------------------------
+# P8: primitive recovery round trip.
+# ---------------------------------------------------------------------------
+def test_fluid_primitive_recovery_round_trip(O):
+    """For P = w rho: E = (rho + P) W^2 - P, J = (rho + P) W^2 v with W^2 = 1/(1 - v^2);
+    the oracle's recovery from (E, J^2) returns rho to rounding (times the
+    problem's condition number), for slow and fast flows and several equations
+    of state."""
+    rng = np.random.default_rng(8)
+    for w in (1.0 / 3.0, 0.1, 1.0):
+        rho = 10.0 ** rng.uniform(-3, 3, 2000)
+        v = np.concatenate([rng.uniform(0, 0.1, 1000), rng.uniform(0.1, 0.99, 1000)])
+        W2 = 1.0 / (1.0 - v * v)
+        P = w * rho
+        E = (rho + P) * W2 - P
+        J = (rho + P) * W2 * v
+        got = O.fluid_rho(E, J * J, w)
+        # E^2 - J^2 = (rho + P)^2 W^2 - ... cancels as v -> 1: the recovery's condition
+        # number grows like W^4, so the bound does too (a wrong formula is off by O(1))
+        assert np.all(np.abs(got - rho) <= 4e-15 * W2 * W2 * rho), (w, np.max(np.abs(got / rho - 1)))
