@@ -161,6 +161,14 @@ int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, in
 int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
                     size_t ws_bytes, void* stream);
 
+/* cosmos_rk4_step that also keeps the step's stage states: U2 = U_n + dt/2 k1,
+ * U3 = U_n + dt/2 k2, U4 = U_n + dt k3 (k_s the right-hand side at stage s),
+ * for cosmos_adjoint_step_stages.  U2, U3, U4: caller-owned device buffers in
+ * state layout, distinct from state and from each other (else COSMOS_EINVAL).
+ * state is updated bitwise as by cosmos_rk4_step.  ws: COSMOS_OP_RK4 bytes. */
+int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt,
+                           double* U2, double* U3, double* U4, void* ws, size_t ws_bytes, void* stream);
+
 /* End-to-end step with HOST buffers: copies host_in (pageable or pinned
  * host memory, cosmos_field_stride * nfields doubles, library layout) to
  * dev_state, runs `steps` RK4 steps (ws: COSMOS_OP_RK4 bytes) and copies the
@@ -209,6 +217,15 @@ int cosmos_rhs_vjp(const cosmos_grid* g, const cosmos_params* p, const double* U
  * lam_n may equal lam_np1 (in place). */
 int cosmos_adjoint_step(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* lam_np1,
                         double* lam_n, double t, double dt, void* ws, size_t ws_bytes, void* stream);
+
+/* cosmos_adjoint_step with the step's stage states U2, U3, U4 supplied (as
+ * written by cosmos_rk4_step_stages from U_n at the same t, dt) instead of
+ * recomputed: three forward stages fewer per step, the same result bitwise.
+ * lam_n may equal lam_np1; it must not alias a state.  ws: COSMOS_OP_ADJOINT
+ * bytes. */
+int cosmos_adjoint_step_stages(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* U2,
+                               const double* U3, const double* U4, const double* lam_np1, double* lam_n, double t,
+                               double dt, void* ws, size_t ws_bytes, void* stream);
 
 /* FLRW initial data (as cosmos_init_grid kind 1) from a per-point curvature
  * perturbation zeta (one double per point, state row layout):

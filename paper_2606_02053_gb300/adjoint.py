@@ -13,7 +13,8 @@ radiation fluid, initial data from a per-point curvature perturbation zeta
 
 ``CosmosAdjoint`` (a torch.autograd.Function) maps zeta -> (min lapse, peak
 compaction); its backward replays each checkpoint segment forward, stores the
-segment's time levels, and runs cosmos_adjoint_step backwards through them,
+segment's time levels and their RK4 stage states (cosmos_rk4_step_stages), and
+runs cosmos_adjoint_step_stages backwards through them,
 injecting the diagnostics' cotangents at the step they were measured, then
 cosmos_init_zeta_vjp.  zeta = mu * profile built with torch gives d/d mu by
 ordinary autograd.
@@ -98,16 +99,20 @@ class CollapseRun:
         for si in reversed(range(len(starts))):
             s0 = starts[si]
             s1 = starts[si + 1] if si + 1 < len(starts) else self.steps
-            levels = [rec["checkpoints"][s0].clone()]
-            U = levels[0].clone()
-            for s in range(s0, s1 - 1):
-                self.step(U, s)
-                levels.append(U.clone())
+            # replay the segment, keeping every step's level and its three stage states
+            U = rec["checkpoints"][s0].clone()
+            saved = []
+            for s in range(s0, s1):
+                stages = [self.new_state() for _ in range(3)]
+                saved.append((U.clone(), stages))
+                C.check(C.cosmos_rk4_step_stages(self.g, self.p, U, s * self.dt, self.dt, *stages, self.ws_rk4))
             for s in reversed(range(s0, s1)):
-                C.check(C.cosmos_adjoint_step(self.g, self.p, levels[s - s0], lam, lam, s * self.dt, self.dt,
-                                              self.ws_adj))
+                Un, (U2, U3, U4) = saved[s - s0]
+                C.check(C.cosmos_adjoint_step_stages(self.g, self.p, Un, U2, U3, U4, lam, lam, s * self.dt, self.dt,
+                                                     self.ws_adj))
                 if s == rec["nstar"]:
                     lam[ALPHA * self.fs + self.centre] += gbar_alpha
+            del saved
         zbar = torch.empty(self.fs, dtype=torch.float64, device=self.device)
         C.check(C.cosmos_init_zeta_vjp(self.g, self.p, rec["U0"], lam, zbar, self.ws_ivjp))
         return zbar

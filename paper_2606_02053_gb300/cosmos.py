@@ -68,6 +68,7 @@ _SIGS = {
     "cosmos_rhs": ([_G, _PP, _P, _P, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_rk4_stage": ([_G, _PP, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_rk4_step": ([_G, _PP, _P, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_rk4_step_stages": ([_G, _PP, _P, _D, _D, _P, _P, _P, _P, _S, _P], ctypes.c_int),
     "cosmos_stage_pass": ([_G, _PP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
@@ -76,6 +77,7 @@ _SIGS = {
     "cosmos_adjoint_workspace_bytes": ([_G, _PP, ctypes.c_int], ctypes.c_size_t),
     "cosmos_rhs_vjp": ([_G, _PP, _P, _P, _P, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_adjoint_step": ([_G, _PP, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_adjoint_step_stages": ([_G, _PP, _P, _P, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_init_zeta": ([_G, _PP, _P, _D, _P, _P, _S, _P], ctypes.c_int),
     "cosmos_init_zeta_vjp": ([_G, _PP, _P, _P, _P, _P, _S, _P], ctypes.c_int),
     "cosmos_compaction": ([_G, _PP, _P, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
@@ -179,6 +181,12 @@ def cosmos_rk4_step(g, p, state, t, dt, ws=None, stream=None) -> int:
                                  _stream(stream))
 
 
+def cosmos_rk4_step_stages(g, p, state, t, dt, U2, U3, U4, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_rk4_step_stages(ctypes.byref(g), ctypes.byref(p), _ptr(state), float(t), float(dt),
+                                        _ptr(U2), _ptr(U3), _ptr(U4), w, nb, _stream(stream))
+
+
 def cosmos_evolve_host(g, p, host_in, host_out, dev_state, steps, t, dt, ws=None, stream=None) -> int:
     w, nb = _ws(ws)
     return lib().cosmos_evolve_host(ctypes.byref(g), ctypes.byref(p), _ptr(host_in), _ptr(host_out),
@@ -218,6 +226,13 @@ def cosmos_adjoint_step(g, p, U_n, lam_np1, lam_n, t, dt, ws=None, stream=None) 
     wp, nb = _ws(ws)
     return lib().cosmos_adjoint_step(ctypes.byref(g), ctypes.byref(p), _ptr(U_n), _ptr(lam_np1), _ptr(lam_n),
                                      float(t), float(dt), wp, nb, _stream(stream))
+
+
+def cosmos_adjoint_step_stages(g, p, U_n, U2, U3, U4, lam_np1, lam_n, t, dt, ws=None, stream=None) -> int:
+    wp, nb = _ws(ws)
+    return lib().cosmos_adjoint_step_stages(ctypes.byref(g), ctypes.byref(p), _ptr(U_n), _ptr(U2), _ptr(U3),
+                                            _ptr(U4), _ptr(lam_np1), _ptr(lam_n), float(t), float(dt), wp, nb,
+                                            _stream(stream))
 
 
 def cosmos_init_zeta(g, p, zeta, a0, state, ws=None, stream=None) -> int:

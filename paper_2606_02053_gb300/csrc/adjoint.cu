@@ -324,24 +324,14 @@ int cosmos_rhs_vjp(const cosmos_grid* g, const cosmos_params* p, const double* U
   return COSMOS_OK;
 }
 
-int cosmos_adjoint_step(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* lam_np1,
-                        double* lam_n, double t, double dt, void* ws, size_t ws_bytes, void* stream) {
-  int e = check_adj(g, p);
-  if (e) return e;
-  if (!U_n || !lam_np1 || !lam_n || lam_n == U_n) return COSMOS_EINVAL;
-  const AdjLayout L = adj_layout(g, p, COSMOS_OP_ADJOINT);
-  if ((e = check_ws_adj(L.total_bytes, ws, ws_bytes))) return e;
-  cudaStream_t s = (cudaStream_t)stream;
-  double* w = (double*)ws;
+// Reverse sweep of one RK4 step given its stage states U2, U3, U4 (U_1 = U_n).
+static int adjoint_sweep(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* U2,
+                         const double* U3, const double* U4, const double* lam_np1, double* lam_n, double t,
+                         double dt, double* w, const AdjLayout& L, cudaStream_t s) {
   const long n = (long)cosmos_field_stride(g) * cosmos_nfields(p);
-  double *U2 = w + L.U2, *U3 = w + L.U3, *U4 = w + L.U4, *KB = w + L.KB, *KB2 = w + L.KB2, *LAM = w + L.LAM;
+  double *KB = w + L.KB, *KB2 = w + L.KB2, *LAM = w + L.LAM;
   const double dt2 = 0.5 * dt;
-  // forward stage states (the same sums as cosmos_rk4_step); KB is scratch here
-  if (fwd_stage(g, p, U_n, U_n, U2, KB, t, dt2, w, L, s) != cudaSuccess ||
-      fwd_stage(g, p, U2, U_n, U3, KB, t + dt2, dt2, w, L, s) != cudaSuccess ||
-      fwd_stage(g, p, U3, U_n, U4, KB, t + dt2, dt, w, L, s) != cudaSuccess)
-    return COSMOS_ECUDA;
-  // reverse sweep:  lam_n = lam + sum_s (dF/dU at U_s)^T kbar_s
+  // lam_n = lam + sum_s (dF/dU at U_s)^T kbar_s
   if (cudaMemcpyAsync(LAM, lam_np1, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return COSMOS_ECUDA;
   if (lam_n != lam_np1 &&
@@ -356,6 +346,37 @@ int cosmos_adjoint_step(const cosmos_grid* g, const cosmos_params* p, const doub
     return COSMOS_ECUDA;
   if (vjp_once(g, p, U_n, t, KB2, lam_n, LAM, nullptr, 0.0, 0.0, w, L, s) != cudaSuccess) return COSMOS_ECUDA;
   return COSMOS_OK;
+}
+
+int cosmos_adjoint_step(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* lam_np1,
+                        double* lam_n, double t, double dt, void* ws, size_t ws_bytes, void* stream) {
+  int e = check_adj(g, p);
+  if (e) return e;
+  if (!U_n || !lam_np1 || !lam_n || lam_n == U_n) return COSMOS_EINVAL;
+  const AdjLayout L = adj_layout(g, p, COSMOS_OP_ADJOINT);
+  if ((e = check_ws_adj(L.total_bytes, ws, ws_bytes))) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* w = (double*)ws;
+  double *U2 = w + L.U2, *U3 = w + L.U3, *U4 = w + L.U4, *KB = w + L.KB;
+  const double dt2 = 0.5 * dt;
+  // forward stage states (the same sums as cosmos_rk4_step); KB is scratch here
+  if (fwd_stage(g, p, U_n, U_n, U2, KB, t, dt2, w, L, s) != cudaSuccess ||
+      fwd_stage(g, p, U2, U_n, U3, KB, t + dt2, dt2, w, L, s) != cudaSuccess ||
+      fwd_stage(g, p, U3, U_n, U4, KB, t + dt2, dt, w, L, s) != cudaSuccess)
+    return COSMOS_ECUDA;
+  return adjoint_sweep(g, p, U_n, U2, U3, U4, lam_np1, lam_n, t, dt, w, L, s);
+}
+
+int cosmos_adjoint_step_stages(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* U2,
+                               const double* U3, const double* U4, const double* lam_np1, double* lam_n, double t,
+                               double dt, void* ws, size_t ws_bytes, void* stream) {
+  int e = check_adj(g, p);
+  if (e) return e;
+  if (!U_n || !U2 || !U3 || !U4 || !lam_np1 || !lam_n) return COSMOS_EINVAL;
+  if (lam_n == U_n || lam_n == U2 || lam_n == U3 || lam_n == U4) return COSMOS_EINVAL;
+  const AdjLayout L = adj_layout(g, p, COSMOS_OP_ADJOINT);
+  if ((e = check_ws_adj(L.total_bytes, ws, ws_bytes))) return e;
+  return adjoint_sweep(g, p, U_n, U2, U3, U4, lam_np1, lam_n, t, dt, (double*)ws, L, (cudaStream_t)stream);
 }
 
 int cosmos_init_zeta(const cosmos_grid* g, const cosmos_params* p, const double* zeta, double a0, double* state,

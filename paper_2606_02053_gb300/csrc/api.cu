@@ -469,6 +469,26 @@ int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state,
   return run_stage(g, p, MODE_S4, A, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s);
 }
 
+int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt,
+                           double* U2, double* U3, double* U4, void* ws, size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state || !U2 || !U3 || !U4) return COSMOS_EINVAL;
+  if (U2 == state || U3 == state || U4 == state || U2 == U3 || U2 == U4 || U3 == U4) return COSMOS_EINVAL;
+  if (!aligned16(state) || !aligned16(U2) || !aligned16(U3) || !aligned16(U4)) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RK4);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  double* w = (double*)ws;
+  double* acc = w + L.acc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double dt2 = 0.5 * dt;
+  // the stages of cosmos_rk4_step, with the stage states kept in U2, U3, U4
+  if ((e = run_stage(g, p, MODE_S1, state, state, U2, acc, t, dt2, 2.0, w, L, s))) return e;
+  if ((e = run_stage(g, p, MODE_S23, U2, state, U3, acc, t + dt2, dt2, 2.0, w, L, s))) return e;
+  if ((e = run_stage(g, p, MODE_S23, U3, state, U4, acc, t + dt2, dt, 2.0, w, L, s))) return e;
+  return run_stage(g, p, MODE_S4, U4, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s);
+}
+
 namespace {
 // Copy stream and events of one cosmos_evolve_host call; destroyed on every
 // return path (work still queued on them completes first).

@@ -222,3 +222,40 @@ def test_checkpointed_gradient_matches_finite_differences_in_mu(C):
     fd_comp = (plus[1] - minus[1]) / (2 * hmu)
     assert abs(float(gmin) - fd_min) <= 1e-6 * abs(fd_min), (float(gmin), fd_min)
     assert abs(float(gcomp) - fd_comp) <= 1e-6 * abs(fd_comp), (float(gcomp), fd_comp)
+
+
+@pytest.mark.parametrize("fluid,scalar", [(0, 0), (1, 1)])
+def test_saved_stage_states_give_the_same_step_and_adjoint(C, fluid, scalar):
+    """cosmos_rk4_step_stages = cosmos_rk4_step (bitwise), its stage states are
+    those of the fused stages, and cosmos_adjoint_step_stages on them =
+    cosmos_adjoint_step (bitwise)."""
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = (20, 14, 12)
+    h = 1.0 / n[0]
+    p = C.make_params(fluid=fluid, scalar=scalar, H0=2.0 * fluid)
+    ev = Evolution(C.make_grid(n, h, pitch=24), p)
+    ev.set_state(inputs.smooth_state(n, seed=5 + fluid, fluid=fluid, scalar=scalar, scale=0.5))
+    U0 = ev.state.clone()
+    t, dt = 0.03, 0.25 * h
+    ev.step(t, dt)
+    ref = ev.state.clone()
+    st = U0.clone()
+    U2, U3, U4 = (torch.empty_like(st) for _ in range(3))
+    C.check(C.cosmos_rk4_step_stages(ev.g, p, st, t, dt, U2, U3, U4, ev.ws_rk4))
+    assert torch.equal(st, ref)
+    # stage 1 of the fused stages writes U2 from U_n
+    A, acc = torch.empty_like(st), torch.empty_like(st)
+    C.check(C.cosmos_rk4_stage(ev.g, p, 1, U0, U0.clone(), A, acc, t, dt, ev.ws_rhs))
+    nx = ev.g.nx  # rows are padded to a pitch of 24; the padding is never written
+    assert torch.equal(ev.view(A)[..., :nx], ev.view(U2)[..., :nx])
+    lam = torch.from_numpy(np.random.default_rng(3).standard_normal(U0.numel())).cuda()
+    a = torch.empty_like(lam)
+    b = torch.empty_like(lam)
+    wsa = ws(C, ev.g, p, C.COSMOS_OP_ADJOINT)
+    C.check(C.cosmos_adjoint_step(ev.g, p, U0, lam, a, t, dt, wsa))
+    C.check(C.cosmos_adjoint_step_stages(ev.g, p, U0, U2, U3, U4, lam, b, t, dt, wsa))
+    assert torch.equal(a, b)
+    assert C.cosmos_adjoint_step_stages(ev.g, p, U0, U2, U3, U4, lam, U2, t, dt, wsa) == C.COSMOS_EINVAL
+    assert C.cosmos_rk4_step_stages(ev.g, p, st, t, dt, U2, U2, U4, ev.ws_rk4) == C.COSMOS_EINVAL
