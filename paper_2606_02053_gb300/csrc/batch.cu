@@ -45,7 +45,7 @@ struct BatchLayout {
   size_t total;
 };
 
-// 32 x 4 tiles of every plane: the derivative pass's work list
+// BX x DBY (32 x 8) tiles of every plane: the derivative pass's work list
 static long deriv_tiles(const cosmos_grid& g) {
   return (long)((g.nx + BX - 1) / BX) * ((g.ny + DBY - 1) / DBY) * ((g.nz + DBZ - 1) / DBZ);
 }

@@ -126,7 +126,7 @@ cudaError_t launch_stage_vac(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_scalar(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid_scalar(const StageArgs& a, int mode, cudaStream_t s);
-// batched stage: derivative pass over the 32 x 4 tile list (dtiles), algebra
+// batched stage: derivative pass over the BX x DBY tile list (dtiles), algebra
 // pass over the tuned work list (tiles, mapping)
 typedef cudaError_t (*BatchStageLauncher)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
                                           dim3, cudaStream_t, const BatchTile*, long);

@@ -437,7 +437,7 @@ __device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g
   return true;
 }
 
-// Persistent batched derivative pass over 32 x 4 tiles of every instance.
+// Persistent batched derivative pass over BX x DBY tiles of every instance.
 template <class T>
 __global__ void __launch_bounds__(BX* DBY* DBZ, COSMOS_DERIV_MIN_BLOCKS)
     batch_deriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
