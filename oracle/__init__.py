@@ -20,6 +20,11 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   fluid_rho   : round trip (rho, v) -> (E, J) -> rho against the definitions.
   rhs_vjp / adjoint_step : tape reverse mode of rhs / rk4_step; pinned by
       finite-difference dot-product tests against the (pinned) forward map.
+  fmr_* (fixed mesh refinement) : prolongation exact for degree-5
+      polynomials and not for degree 6; injection against its definition;
+      the RK4 continuous extension against quadrature and linear-ODE closed
+      forms; the gauge wave on three levels converges at 4th order; an
+      independent copy of the scheme written in the test agrees with it.
 """
 from __future__ import annotations
 
@@ -256,3 +261,90 @@ def flop_count(g: OGrid, params, state, t=0.0):
     n, h, x0 = g.c()
     lib().oracle_flop_count(n, h, x0, _dp(params), _dp(state), float(t), _dp(c))
     return dict(zip(["add", "mul", "div", "sqrt", "cmp"], c.tolist()))
+
+
+# --------------------------------------------------------------------------
+# Fixed mesh refinement (levels described by plain dicts: n, h, x0, origin,
+# lo, hi per level, as paper_2606_02053_gb300.inputs.nested_boxes returns)
+# --------------------------------------------------------------------------
+def _hier_c(levels):
+    L = len(levels)
+    n = (ctypes.c_int * (3 * L))(*[int(v) for lv in levels for v in lv["n"]])
+    h = (ctypes.c_double * (3 * L))(*[float(v) for lv in levels for v in lv["h"]])
+    x0 = (ctypes.c_double * (3 * L))(*[float(v) for lv in levels for v in lv["x0"]])
+    og = (ctypes.c_int * (3 * L))(*[int(v) for lv in levels for v in lv["origin"]])
+    lo = (ctypes.c_int * (3 * L))(*[int(v) for lv in levels for v in lv["lo"]])
+    hi = (ctypes.c_int * (3 * L))(*[int(v) for lv in levels for v in lv["hi"]])
+    return L, n, h, x0, og, lo, hi
+
+
+def _fmr_lib():
+    L = lib()
+    if not getattr(L, "_fmr_sigs", False):
+        H = [ctypes.c_int, _I, _D, _D, _I, _I, _I]
+        L.oracle_fmr_step.argtypes = H + [_D, ctypes.POINTER(_D), ctypes.c_double, ctypes.c_double]
+        L.oracle_fmr_init.argtypes = H + [_D, _D, ctypes.POINTER(_D)]
+        L.oracle_fmr_prolong.argtypes = H + [ctypes.c_int, ctypes.c_int, _D, _D]
+        L.oracle_fmr_restrict.argtypes = H + [ctypes.c_int, ctypes.c_int, _D, _D]
+        L.oracle_rk4_dense.argtypes = [ctypes.c_long, _D, _D, ctypes.c_double, ctypes.c_double, _D]
+        L._fmr_sigs = True
+    return L
+
+
+def level_grid(level) -> OGrid:
+    return OGrid(level["n"], level["h"], level["x0"])
+
+
+def _check_levels(levels, params, states):
+    assert len(states) == len(levels)
+    for lv, s in zip(levels, states):
+        _check_state(level_grid(lv), params, s)
+
+
+def fmr_init(levels, params, idarr):
+    """Initial data on every level of the hierarchy; returns the list of states."""
+    states = [np.empty((nfields(params), lv["n"][2], lv["n"][1], lv["n"][0])) for lv in levels]
+    ptrs = (_D * len(levels))(*[_dp(s) for s in states])
+    _fmr_lib().oracle_fmr_init(*_hier_c(levels), _dp(params), _dp(np.asarray(idarr, dtype=np.float64)), ptrs)
+    return states
+
+
+def fmr_step(levels, params, states, t, dt0):
+    """In place: one step of the hierarchy (level l takes 2^l steps of dt0 / 2^l)."""
+    _check_levels(levels, params, states)
+    ptrs = (_D * len(levels))(*[_dp(s) for s in states])
+    _fmr_lib().oracle_fmr_step(*_hier_c(levels), _dp(params), ptrs, float(t), float(dt0))
+    return states
+
+
+def fmr_prolong(levels, level, parent, child):
+    """In place: ghost points of `child` (level `level`) from the parent state."""
+    nf = parent.shape[0]
+    assert parent.flags.c_contiguous and child.flags.c_contiguous and child.shape[0] == nf
+    _fmr_lib().oracle_fmr_prolong(*_hier_c(levels), int(level), nf, _dp(parent), _dp(child))
+    return child
+
+
+def fmr_restrict(levels, level, child, parent):
+    """In place: interior points of `child` lying on parent points overwrite them."""
+    nf = parent.shape[0]
+    assert parent.flags.c_contiguous and child.flags.c_contiguous and child.shape[0] == nf
+    _fmr_lib().oracle_fmr_restrict(*_hier_c(levels), int(level), nf, _dp(child), _dp(parent))
+    return parent
+
+
+def rk4_dense(Un, k, dt, theta):
+    """U_n + dt sum_s b_s(theta) k_s for k = [k1, k2, k3, k4] (arrays like Un)."""
+    Un = np.ascontiguousarray(Un, dtype=np.float64)
+    kk = np.ascontiguousarray(np.stack([np.asarray(x, dtype=np.float64) for x in k]))
+    out = np.empty_like(Un)
+    _fmr_lib().oracle_rk4_dense(Un.size, _dp(Un), _dp(kk), float(dt), float(theta), _dp(out))
+    return out
+
+
+def fmr_interior(level):
+    """Boolean mask [nz, ny, nx] of the interior points of a level."""
+    n, lo, hi = level["n"], level["lo"], level["hi"]
+    m = np.zeros((n[2], n[1], n[0]), dtype=bool)
+    m[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
+    return m

@@ -993,7 +993,8 @@ void rk4_step(const Grid& g, const Params& P, double* state, double t, double dt
 /*          rho_phi = 1/2 chi gt^ij d_i phi d_j phi (fluid and scalar on).  */
 /* id[] = {kind, A, mu, sigma, q0, q1, q2, c0, c1, c2, a0, t}               */
 /* ------------------------------------------------------------------------ */
-void init_all(const Grid& g, const Params& P, const double* id, double* state) {
+/* Lx: wavelength of the gauge wave (0: the grid's own length n_x h_x). */
+void init_all(const Grid& g, const Params& P, const double* id, double* state, double Lx_wave = 0.0) {
   const int kind = (int)id[0];
   const long N = g.npts();
   const int nf = P.nf();
@@ -1007,7 +1008,7 @@ void init_all(const Grid& g, const Params& P, const double* id, double* state) {
         double v[NBSSN];
         for (int f = 0; f < NBSSN; ++f) v[f] = 0.0;
         if (kind == 0) {
-          double A = id[1], Lx = g.n[0] * g.h[0];
+          double A = id[1], Lx = Lx_wave > 0.0 ? Lx_wave : g.n[0] * g.h[0];
           double ph = 2.0 * PI * (x[0] - t) / Lx;
           double H = 1.0 - A * std::sin(ph);
           double dtH = A * (2.0 * PI / Lx) * std::cos(ph);
@@ -1073,6 +1074,295 @@ void init_all(const Grid& g, const Params& P, const double* id, double* state) {
       state[q * N + m] = E[m] / (chi * std::sqrt(chi));
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fixed mesh refinement (section "Statement of need": a fixed set of       */
+/* nested refinement levels resolves the collapsing region; the figure of   */
+/* the lapse at horizon formation shows the lowest level and two refined    */
+/* ones).  The paper gives no scheme for it; the readings taken here:       */
+/*  - level 0 is the periodic box; level l >= 1 is one box of points with   */
+/*    spacing h_l = h_{l-1}/2 whose point 0 lies at x0_{l-1} + origin h_l,  */
+/*    so that every other point of level l sits on a point of level l-1;    */
+/*  - the points of level l outside its interior box [lo, hi) are ghost     */
+/*    points (at least 3 layers, the reach of the Kreiss-Oliger stencil),   */
+/*    set from level l-1 before every RK4 stage; along an axis on which     */
+/*    level l-1 is periodic, level l may instead be periodic too (lo = 0,   */
+/*    hi = n = 2 n_{l-1}, origin 0);                                        */
+/*  - ghost values in space: the tensor product of 1D Lagrange interpolation*/
+/*    through the 6 nearest parent points (degree 5) where the child point  */
+/*    falls half-way between parent points, the parent value where it       */
+/*    falls on one;                                                         */
+/*  - in time (Berger-Oliger subcycling: level l takes two steps of         */
+/*    dt_{l-1}/2 after each step of level l-1): the continuous extension of */
+/*    order 3 of classic RK4 over the parent's step,                        */
+/*      U(t + theta dt) = U_n + dt sum_s b_s(theta) k_s,                     */
+/*      b_1 = theta - 3/2 theta^2 + 2/3 theta^3,                             */
+/*      b_2 = b_3 = theta^2 - 2/3 theta^3,  b_4 = -1/2 theta^2 + 2/3 theta^3 */
+/*    (the polynomials that satisfy the order conditions sum b_s = theta,   */
+/*    sum b_s c_s = theta^2/2, sum b_s c_s^2 = theta^3/3 and                 */
+/*    sum b_s a_sr c_r = theta^3/6 for c = (0, 1/2, 1/2, 1));               */
+/*  - after the two substeps, the interior points of level l that lie on   */
+/*    points of level l-1 overwrite those values (injection).               */
+/* The right-hand side of a level >= 1 is evaluated at its interior points */
+/* only; their stencils (reach 3) stay inside the level's own array.        */
+/* ------------------------------------------------------------------------ */
+constexpr int FMR_MAXL = 8;
+
+struct Hier {
+  int L;
+  Grid g[FMR_MAXL];
+  long origin[FMR_MAXL][3], lo[FMR_MAXL][3], hi[FMR_MAXL][3];
+  bool per[FMR_MAXL][3];  // axis periodic on this level
+};
+
+Hier make_hier(int L, const int* n, const double* h, const double* x0, const int* origin, const int* lo,
+               const int* hi) {
+  Hier H;
+  H.L = L;
+  for (int l = 0; l < L; ++l) {
+    H.g[l] = make_grid(n + 3 * l, h + 3 * l, x0 + 3 * l);
+    for (int d = 0; d < 3; ++d) {
+      H.origin[l][d] = l ? origin[3 * l + d] : 0;
+      H.lo[l][d] = l ? lo[3 * l + d] : 0;
+      H.hi[l][d] = l ? hi[3 * l + d] : n[3 * l + d];
+      H.per[l][d] = l == 0 || (H.per[l - 1][d] && H.lo[l][d] == 0 && H.hi[l][d] == n[3 * l + d] &&
+                               H.origin[l][d] == 0 && n[3 * l + d] == 2 * n[3 * (l - 1) + d]);
+    }
+  }
+  return H;
+}
+
+bool interior(const Hier& H, int l, long i, long j, long k) {
+  const long q[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d)
+    if (q[d] < H.lo[l][d] || q[d] >= H.hi[l][d]) return false;
+  return true;
+}
+
+inline long floordiv2(long a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+
+/* Lagrange weights at x = 0 for nodes x_m = m - 2.5, m = 0..5 (the six parent
+ * points around a half-way child point, in parent spacings). */
+void lagrange6_half(double w[6]) {
+  for (int m = 0; m < 6; ++m) {
+    double num = 1.0, den = 1.0;
+    const double xm = m - 2.5;
+    for (int q = 0; q < 6; ++q) {
+      if (q == m) continue;
+      const double xq = q - 2.5;
+      num = num * (0.0 - xq);
+      den = den * (xm - xq);
+    }
+    w[m] = num / den;
+  }
+}
+
+/* Parent taps of child index i along axis d of level l (1 or 6 points). */
+int parent_taps(const Hier& H, int l, int d, long i, long idx[6], double w[6]) {
+  const long X2 = H.origin[l][d] + i;  // child point position in child spacings from parent point 0
+  const long np = H.g[l - 1].n[d];
+  if (X2 % 2 == 0) {
+    idx[0] = X2 / 2;
+    w[0] = 1.0;
+  } else {
+    const long base = floordiv2(X2);  // parent point just below
+    lagrange6_half(w);
+    for (int m = 0; m < 6; ++m) idx[m] = base - 2 + m;
+  }
+  const int nt = (X2 % 2 == 0) ? 1 : 6;
+  if (H.per[l - 1][d])
+    for (int m = 0; m < nt; ++m) idx[m] = wrapi(idx[m], np);
+  return nt;
+}
+
+/* Ghost points of level l from a parent state P (level l-1 layout). */
+void prolong(const Hier& H, int l, int nf, const double* P, double* C) {
+  const Grid& gc = H.g[l];
+  const Grid& gp = H.g[l - 1];
+  const long Nc = gc.npts(), Np = gp.npts();
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < gc.n[2]; ++k)
+    for (long j = 0; j < gc.n[1]; ++j)
+      for (long i = 0; i < gc.n[0]; ++i) {
+        if (interior(H, l, i, j, k)) continue;
+        long ix[6], iy[6], iz[6];
+        double wx[6], wy[6], wz[6];
+        const int nx = parent_taps(H, l, 0, i, ix, wx);
+        const int ny = parent_taps(H, l, 1, j, iy, wy);
+        const int nz = parent_taps(H, l, 2, k, iz, wz);
+        const long c = (k * gc.n[1] + j) * gc.n[0] + i;
+        for (int f = 0; f < nf; ++f) {
+          double s = 0.0;
+          for (int c3 = 0; c3 < nz; ++c3)
+            for (int b = 0; b < ny; ++b)
+              for (int a = 0; a < nx; ++a)
+                s = s + wz[c3] * wy[b] * wx[a] * P[f * Np + (iz[c3] * gp.n[1] + iy[b]) * gp.n[0] + ix[a]];
+          C[f * Nc + c] = s;
+        }
+      }
+}
+
+/* Interior points of level l lying on level l-1 points overwrite those. */
+void restrict_to_parent(const Hier& H, int l, int nf, const double* C, double* P) {
+  const Grid& gc = H.g[l];
+  const Grid& gp = H.g[l - 1];
+  const long Nc = gc.npts(), Np = gp.npts();
+  for (long k = H.lo[l][2]; k < H.hi[l][2]; ++k)
+    for (long j = H.lo[l][1]; j < H.hi[l][1]; ++j)
+      for (long i = H.lo[l][0]; i < H.hi[l][0]; ++i) {
+        const long q[3] = {i, j, k};
+        long pq[3];
+        bool on = true;
+        for (int d = 0; d < 3; ++d) {
+          const long X2 = H.origin[l][d] + q[d];
+          if (X2 % 2 != 0) on = false;
+          pq[d] = H.per[l - 1][d] ? wrapi(floordiv2(X2), gp.n[d]) : floordiv2(X2);
+        }
+        if (!on) continue;
+        const long cc = (k * gc.n[1] + j) * gc.n[0] + i;
+        const long pc = (pq[2] * gp.n[1] + pq[1]) * gp.n[0] + pq[0];
+        for (int f = 0; f < nf; ++f) P[f * Np + pc] = C[f * Nc + cc];
+      }
+}
+
+/* The continuous extension of RK4: out = U_n + dt sum_s b_s(theta) k_s. */
+void rk4_dense(long M, const double* Un, const double* const k[4], double dt, double theta, double* out) {
+  const double t2 = theta * theta, t3 = t2 * theta;
+  const double b[4] = {theta - 1.5 * t2 + 2.0 / 3.0 * t3, t2 - 2.0 / 3.0 * t3, t2 - 2.0 / 3.0 * t3,
+                       -0.5 * t2 + 2.0 / 3.0 * t3};
+  for (long m = 0; m < M; ++m)
+    out[m] = Un[m] + dt * (b[0] * k[0][m] + b[1] * k[1][m] + b[2] * k[2][m] + b[3] * k[3][m]);
+}
+
+/* One parent step kept for the child's ghost values. */
+struct Saved {
+  std::vector<double> Un, k[4];
+  double dt;
+};
+
+/* Right-hand side at the interior points of level l (zero at ghost points). */
+void rhs_level(const Hier& H, const Params& P, int l, const double* state, double t, double* rhs) {
+  const Grid& g = H.g[l];
+  Field F{&g, state};
+  const int nf = P.nf();
+  const long N = g.npts();
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        const long idx = (k * g.n[1] + j) * g.n[0] + i;
+        if (!interior(H, l, i, j, k)) {
+          for (int f = 0; f < nf; ++f) rhs[f * N + idx] = 0.0;
+          continue;
+        }
+        double out[NFMAX];
+        Pt p{{i, j, k}};
+        point_rhs<double>(F, P, p, t, out);
+        for (int f = 0; f < nf; ++f) rhs[f * N + idx] = out[f];
+      }
+}
+
+/* Ghost values of the RK4 stages of a child substep.  The stage states of
+ * classic RK4 applied to a solution u with time derivatives u1 = u',
+ * u2 = u'', u3 = u''' at the substep's start (step tau) are, to the order
+ * that matters here,
+ *   Y_1 = u,  Y_2 = u + tau/2 u1,  Y_3 = u + tau/2 u1 + tau^2/4 u2,
+ *   Y_4 = u + tau u1 + tau^2/2 u2 + tau^3/4 u3
+ * (exact for a linear autonomous system: Y_2 = u + tau/2 L u, Y_3 = u +
+ * tau/2 L Y_2, Y_4 = u + tau L Y_3).  Setting the ghost points of stage s to
+ * Y_s built from the parent's continuous extension u(theta), instead of to u
+ * at the stage time, keeps the ghost data consistent with the interior's
+ * stage states (the stage-consistent interpolation of McCorquodale and
+ * Colella, 2011); plain values at the stage times lose about one order.
+ * With tau = r dt_parent and d/dt = (1/dt_parent) d/dtheta, the ghost value
+ * of stage s is U_n + dt_parent sum_q beta_q k_q, beta built from b_q(theta0)
+ * and its theta-derivatives. */
+void ghost_stage_coeffs(double theta0, int stage, double r, double beta[4]) {
+  const double th = theta0, t2 = th * th, t3 = t2 * th;
+  // b_q(theta) of the continuous extension and its first three derivatives
+  const double b0[4] = {th - 1.5 * t2 + 2.0 / 3.0 * t3, t2 - 2.0 / 3.0 * t3, t2 - 2.0 / 3.0 * t3,
+                        -0.5 * t2 + 2.0 / 3.0 * t3};
+  const double b1[4] = {1.0 - 3.0 * th + 2.0 * t2, 2.0 * th - 2.0 * t2, 2.0 * th - 2.0 * t2, -th + 2.0 * t2};
+  const double b2[4] = {-3.0 + 4.0 * th, 2.0 - 4.0 * th, 2.0 - 4.0 * th, -1.0 + 4.0 * th};
+  const double b3[4] = {4.0, -4.0, -4.0, 4.0};
+  double c1 = 0.0, c2 = 0.0, c3 = 0.0;  // weights of the first, second, third theta-derivative
+  if (stage == 2) c1 = r / 2.0;
+  if (stage == 3) {
+    c1 = r / 2.0;
+    c2 = r * r / 4.0;
+  }
+  if (stage == 4) {
+    c1 = r;
+    c2 = r * r / 2.0;
+    c3 = r * r * r / 4.0;
+  }
+  for (int q = 0; q < 4; ++q) beta[q] = b0[q] + c1 * b1[q] + c2 * b2[q] + c3 * b3[q];
+}
+
+/* Ghost points of level l for stage `stage` of its substep that starts at
+ * theta0 of the parent's saved step (child step = half the parent's). */
+void fill_ghosts(const Hier& H, const Params& P, int l, const Saved& S, double theta0, int stage, double* C) {
+  const long Mp = (long)P.nf() * H.g[l - 1].npts();
+  double beta[4];
+  ghost_stage_coeffs(theta0, stage, 0.5, beta);
+  std::vector<double> Y(Mp);
+  for (long m = 0; m < Mp; ++m)
+    Y[m] = S.Un[m] + S.dt * (beta[0] * S.k[0][m] + beta[1] * S.k[1][m] + beta[2] * S.k[2][m] +
+                             beta[3] * S.k[3][m]);
+  prolong(H, l, P.nf(), Y.data(), C);
+}
+
+/* One step of level l from t (starting at theta0 of the parent's step)
+ * followed, when level l+1 exists, by its two substeps and the injection. */
+void fmr_advance(const Hier& H, const Params& P, double* const* U, std::vector<Saved>& S, int l, double t,
+                 double dt, double theta0) {
+  const long M = (long)P.nf() * H.g[l].npts();
+  double* u = U[l];
+  std::vector<double> k[4], Y(M);
+  for (int s = 0; s < 4; ++s) k[s].resize(M);
+  auto ghosts = [&](double* X, int stage) {
+    if (l > 0) fill_ghosts(H, P, l, S[l - 1], theta0, stage, X);
+  };
+  ghosts(u, 1);
+  std::vector<double> Un(u, u + M);
+  rhs_level(H, P, l, Un.data(), t, k[0].data());
+  for (long m = 0; m < M; ++m) Y[m] = Un[m] + 0.5 * dt * k[0][m];
+  ghosts(Y.data(), 2);
+  rhs_level(H, P, l, Y.data(), t + 0.5 * dt, k[1].data());
+  for (long m = 0; m < M; ++m) Y[m] = Un[m] + 0.5 * dt * k[1][m];
+  ghosts(Y.data(), 3);
+  rhs_level(H, P, l, Y.data(), t + 0.5 * dt, k[2].data());
+  for (long m = 0; m < M; ++m) Y[m] = Un[m] + dt * k[2][m];
+  ghosts(Y.data(), 4);
+  rhs_level(H, P, l, Y.data(), t + dt, k[3].data());
+  for (long m = 0; m < M; ++m) u[m] = Un[m] + dt / 6.0 * (k[0][m] + 2.0 * k[1][m] + 2.0 * k[2][m] + k[3][m]);
+  if (l + 1 < H.L) {
+    S[l].Un = Un;
+    for (int s = 0; s < 4; ++s) S[l].k[s] = k[s];
+    S[l].dt = dt;
+    fmr_advance(H, P, U, S, l + 1, t, 0.5 * dt, 0.0);
+    fmr_advance(H, P, U, S, l + 1, t + 0.5 * dt, 0.5 * dt, 0.5);
+    restrict_to_parent(H, l + 1, P.nf(), U[l + 1], u);
+  }
+}
+
+/* One step of the hierarchy (level 0 by dt0, level l by 2^l steps of
+ * dt0/2^l), then the ghost points of every level from its parent's new state. */
+void fmr_step(const Hier& H, const Params& P, double* const* U, double t, double dt0) {
+  std::vector<Saved> S(H.L);
+  fmr_advance(H, P, U, S, 0, t, dt0, 0.0);
+  for (int l = 1; l < H.L; ++l) prolong(H, l, P.nf(), U[l - 1], U[l]);
+}
+
+/* Initial data on every level (each from its own points and discrete
+ * constraint), injection from the finest level down, then the ghost points
+ * of every level from its parent. */
+void fmr_init(const Hier& H, const Params& P, const double* id, double* const* U) {
+  const double Lx = H.g[0].n[0] * H.g[0].h[0];  // the gauge wave's wavelength is the periodic box
+  for (int l = 0; l < H.L; ++l) init_all(H.g[l], P, id, U[l], Lx);
+  for (int l = H.L - 1; l >= 1; --l) restrict_to_parent(H, l, P.nf(), U[l], U[l - 1]);
+  for (int l = 1; l < H.L; ++l) prolong(H, l, P.nf(), U[l - 1], U[l]);
 }
 
 }  // namespace
@@ -1292,6 +1582,42 @@ void oracle_flop_count_parts(const int* n, const double* h, const double* x0, co
     }
   }
   snap(3);
+}
+
+/* Fixed mesh refinement.  Hierarchy of L levels: per level l, n[3l..3l+2],
+ * h[3l..], x0[3l..], origin[3l..], lo[3l..], hi[3l..] (origin, lo, hi are
+ * ignored for level 0).  states[l]: level l state, oracle layout. */
+void oracle_fmr_step(int L, const int* n, const double* h, const double* x0, const int* origin, const int* lo,
+                     const int* hi, const double* params, double* const* states, double t, double dt0) {
+  Hier H = make_hier(L, n, h, x0, origin, lo, hi);
+  fmr_step(H, unpack_params(params), states, t, dt0);
+}
+
+void oracle_fmr_init(int L, const int* n, const double* h, const double* x0, const int* origin, const int* lo,
+                     const int* hi, const double* params, const double* id, double* const* states) {
+  Hier H = make_hier(L, n, h, x0, origin, lo, hi);
+  fmr_init(H, unpack_params(params), id, states);
+}
+
+/* Ghost points of level `level` from the parent state `parent` (nf fields). */
+void oracle_fmr_prolong(int L, const int* n, const double* h, const double* x0, const int* origin, const int* lo,
+                        const int* hi, int level, int nf, const double* parent, double* child) {
+  Hier H = make_hier(L, n, h, x0, origin, lo, hi);
+  prolong(H, level, nf, parent, child);
+}
+
+/* Injection of level `level`'s interior into its parent (nf fields). */
+void oracle_fmr_restrict(int L, const int* n, const double* h, const double* x0, const int* origin, const int* lo,
+                         const int* hi, int level, int nf, const double* child, double* parent) {
+  Hier H = make_hier(L, n, h, x0, origin, lo, hi);
+  restrict_to_parent(H, level, nf, child, parent);
+}
+
+/* Continuous extension of one RK4 step: out = U_n + dt sum_s b_s(theta) k_s
+ * over M values (k = k1..k4 stacked, 4 M values). */
+void oracle_rk4_dense(long M, const double* Un, const double* k, double dt, double theta, double* out) {
+  const double* ks[4] = {k, k + M, k + 2 * M, k + 3 * M};
+  rk4_dense(M, Un, ks, dt, theta, out);
 }
 
 }  // extern "C"

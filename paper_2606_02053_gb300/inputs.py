@@ -105,3 +105,52 @@ def scan_instances(count=64, seed=2606, n_lo=64, n_hi=96, L=1.0):
 # Workload descriptions (plain data).
 GAUGE_WAVE = dict(A=0.01, L=1.0, cfl=0.25)
 FLRW_ZETA = dict(w=1.0 / 3.0, mu=0.5, sigma_over_L=1.0 / 8.0, H0_times_L=40.0, cfl=0.25)
+
+
+def nested_boxes(n0, h0, x0, levels, n_child, centre=None):
+    """Plain description of a fixed-mesh-refinement hierarchy of nested boxes.
+
+    Level 0: the periodic box of n0 = (nx, ny, nz) points, spacing h0, point 0
+    at x0.  Level l >= 1: an array of n_child[l-1] = (nx, ny, nz) points (an int
+    gives a cube) with spacing h0 / 2^l.  Along each axis it is either periodic
+    (n = 2 x the parent's points, when the parent is periodic there) or a box
+    whose interior [lo, hi) holds an odd number of points centred on the
+    parent's centre point, with 3 ghost layers below and 3 or 4 above.
+    centre: level-0 index of the centre point (default n0 // 2 per axis).
+
+    Returns a list of per-level dicts: n, h, x0, origin, lo, hi (origin is
+    the position of the level's point 0 on its parent, in the level's own
+    spacing: x0_l = x0_{l-1} + origin * h_l).
+    """
+    n0 = (n0,) * 3 if np.isscalar(n0) else tuple(int(v) for v in n0)
+    c_prev = [n0[d] // 2 for d in range(3)] if centre is None else list(centre)
+    out = [dict(n=n0, h=(h0,) * 3, x0=tuple(float(v) for v in x0), origin=(0, 0, 0), lo=(0, 0, 0), hi=n0,
+                periodic=(True, True, True))]
+    for l in range(1, levels):
+        nc = n_child[l - 1]
+        nc = (nc,) * 3 if np.isscalar(nc) else tuple(int(v) for v in nc)
+        par = out[-1]
+        h = par["h"][0] / 2.0
+        origin, lo, hi, per, c_new = [], [], [], [], []
+        for d in range(3):
+            if par["periodic"][d] and nc[d] == 2 * par["n"][d]:
+                origin.append(0)
+                lo.append(0)
+                hi.append(nc[d])
+                per.append(True)
+                c_new.append(2 * c_prev[d])
+            else:
+                if nc[d] < 8:
+                    raise ValueError("a refined box needs at least 8 points per axis")
+                a, b = 3, nc[d] - 3 - (1 if (nc[d] - 6) % 2 == 0 else 0)
+                cc = a + (b - a - 1) // 2
+                origin.append(2 * c_prev[d] - cc)
+                lo.append(a)
+                hi.append(b)
+                per.append(False)
+                c_new.append(cc)
+        x0l = tuple(par["x0"][d] + origin[d] * h for d in range(3))
+        out.append(dict(n=nc, h=(h,) * 3, x0=x0l, origin=tuple(origin), lo=tuple(lo), hi=tuple(hi),
+                        periodic=tuple(per)))
+        c_prev = c_new
+    return out
