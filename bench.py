@@ -73,16 +73,19 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "scan", "adjoint", "flrw"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "scan", "adjoint", "flrw", "fmr"],
                     help="sweep: single 256^3 grid (headline); scan: 64-instance batched threshold scan; "
                          "adjoint: gradients of collapse diagnostics at 96^3; flrw: 128^3 FLRW + zeta, "
-                         "200 steps, constraint norms")
+                         "200 steps, constraint norms; fmr: 128^3 FLRW + zeta with two nested 96^3 "
+                         "refinement levels")
     ap.add_argument("--adjoint-steps", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-grid", type=int, default=96, help=argparse.SUPPRESS)
     ap.add_argument("--instances", type=int, default=64, help=argparse.SUPPRESS)
     a = ap.parse_args()
     if a.steps is None:
         a.steps = 150 if a.workload == "scan" and a.impl != "reference" else 20
+        if a.workload == "fmr":
+            a.steps = 16
     return a
 
 
@@ -129,6 +132,95 @@ def flrw_workload(args):
                                              "Linf_My", "Linf_Mz"],
                                  "rows": [[s] + v for s, v in norms]},
             "gpu_launches": steps * 4 * 4}  # per stage: primitives, face fluxes, derivative, algebra passes
+    print(json.dumps(line), flush=True)
+
+
+def fmr_workload(args):
+    """Fixed mesh refinement: 128^3 radiation FLRW + Gaussian zeta (mu = 0.5,
+    sigma = L/8, H0 L = 40, w = 1/3) on level 0 and two nested 96^3 levels
+    (89^3 interior points each, spacings h/2 and h/4) centred on the
+    perturbation; one step = one level-0 step of dt = h/4 with 2 and 4
+    substeps of levels 1 and 2.  Reports interior grid-point RK4 updates per
+    second over all levels, the same level arrays stepped as plain periodic
+    grids (no ghost filling or injection) for the overhead, and the interior
+    constraint norms of every level at the start and the end."""
+    import numpy as np
+    import torch
+
+    from paper_2606_02053_gb300 import build, inputs
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.evolve import Evolution
+    from paper_2606_02053_gb300.fmr import Hierarchy
+
+    build.build()
+    n0, nc, nlev = 128, 96, 3
+    h0 = 1.0 / n0
+    lv = inputs.nested_boxes(n0, h0, (-(n0 // 2) * h0,) * 3, nlev, [nc] * (nlev - 1))
+    p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
+    H = Hierarchy(lv, p, pitch_align=32)
+    ident = C.make_id(1, mu=0.5, sigma=0.125)
+    dt0 = 0.25 * h0
+    stream = torch.cuda.current_stream()
+
+    def interior_norms():
+        out = []
+        for l in range(nlev):
+            ev = Evolution(H.grid(l), p)
+            ev.state.copy_(H.states[l])
+            hm, _ = ev.constraints(want_fields=True)
+            lo, hi = lv[l]["lo"], lv[l]["hi"]
+            v = hm[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].reshape(4, -1)
+            out.append([float(np.sqrt((v[m] ** 2).mean())) for m in range(4)])
+            del ev
+        return out
+
+    H.init(ident)
+    H.step(0.0, dt0, max(args.warmup, 1))
+    H.init(ident)
+    norms0 = interior_norms()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    H.step(0.0, dt0, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    norms1 = interior_norms()
+    interior = sum(H.interior_points(l) * 2 ** l for l in range(nlev))
+    arrays = sum(lv[l]["n"][0] * lv[l]["n"][1] * lv[l]["n"][2] * 2 ** l for l in range(nlev))
+    # the same level arrays stepped as plain periodic grids, as many steps each
+    evs = [Evolution(H.grid(l), p) for l in range(nlev)]
+    for l, ev in enumerate(evs):
+        ev.state.copy_(H.states[l])
+        ev.step(0.0, dt0 / 2 ** l, 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(args.steps):
+        for l, ev in enumerate(evs):
+            ev.step(0.0, dt0 / 2 ** l, 2 ** l)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    del evs
+    value = interior * args.steps / (ms * 1e-3)
+    launches_per_level_step = 16  # 4 stages x (primitives, face fluxes, derivative, algebra)
+    launches = sum(2 ** l * (launches_per_level_step + (8 if l else 0)) for l in range(nlev))
+    launches += sum(2 ** (l - 1) for l in range(1, nlev)) + 2 * (nlev - 1)  # injections, final ghost fills
+    line = {"metric": "FP64 interior grid-point RK4 updates/sec, 128^3 FLRW + zeta with 2 nested 96^3 levels",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fmr_flrw_zeta_128^3_plus_2x96^3_levels", "levels": nlev, "grid": n0,
+                       "level_arrays": [list(v["n"]) for v in lv], "interior": [H.interior_points(l)
+                                                                               for l in range(nlev)],
+                       "mu": 0.5, "sigma": 0.125, "H0L": 40.0, "dt_over_h": 0.25,
+                       "interior_updates_per_step": interior, "array_updates_per_step": arrays},
+            "plain_level_steps": {"ms_per_step": ms_plain / args.steps,
+                                  "fmr_overhead": ms / ms_plain - 1.0},
+            "interior_constraint_norms_L2": {"columns": ["level", "H", "Mx", "My", "Mz"],
+                                             "start": [[l] + v for l, v in enumerate(norms0)],
+                                             "end": [[l] + v for l, v in enumerate(norms1)]},
+            "gpu_launches": launches * args.steps}
     print(json.dumps(line), flush=True)
 
 
@@ -420,6 +512,8 @@ def main():
         return adjoint_workload(args)
     if args.workload == "flrw":
         return flrw_workload(args)
+    if args.workload == "fmr":
+        return fmr_workload(args)
 
     import numpy as np
     import torch

@@ -304,6 +304,71 @@ int cosmos_batch_time_stage(cosmos_batch plan, int reps, double* ms_out, void* s
 
 void cosmos_batch_free(cosmos_batch plan);
 
+/* ------------------------------------------------------------------------
+ * Fixed mesh refinement (section "Statement of need": nested refinement
+ * levels resolve the collapsing region; the paper's figure of the lapse at
+ * horizon formation shows the lowest level and two refined ones).  The paper
+ * gives no scheme; this one:
+ *  - level 0 is the periodic box grid[0]; level l >= 1 is one box grid[l]
+ *    with h = h_{l-1}/2 (exactly) and x0 = x0_{l-1} + origin[l] * h, so that
+ *    every other point of level l lies on a point of level l-1;
+ *  - along each axis, level l is either a box with interior [lo, hi),
+ *    lo >= 3 and n - hi >= 3 ghost layers, or, where level l-1 is periodic,
+ *    periodic too (lo = 0, hi = n = 2 n_{l-1}, origin = 0);
+ *  - ghost points are set before every RK4 stage from level l-1: in time from
+ *    the continuous extension of order 3 of the parent's RK4 step, in the
+ *    stage-consistent form (the stage states RK4 forms from the solution's
+ *    Taylor expansion at the substep's start); in space by the tensor product
+ *    of 6-point Lagrange interpolation at half-way points and injection at
+ *    coincident points.  The parent points these read must lie in the
+ *    parent's interior (or wrap on a periodic parent axis), else EINVAL;
+ *  - Berger-Oliger subcycling: level l takes two steps of dt_{l-1}/2 after
+ *    each step of level l-1, then its interior points that lie on level l-1
+ *    points overwrite those (injection);
+ *  - after a hierarchy step every level's ghost points hold the values
+ *    interpolated from its parent's new state.
+ * States use the layout of cosmos_grid for each level (ghost points
+ * included); the right-hand side is exact at interior points only.
+ * ------------------------------------------------------------------------ */
+#define COSMOS_FMR_MAX_LEVELS 8
+
+typedef struct {
+  int levels;                                  /* 1 .. COSMOS_FMR_MAX_LEVELS */
+  cosmos_grid grid[COSMOS_FMR_MAX_LEVELS];     /* per level */
+  int origin[COSMOS_FMR_MAX_LEVELS][3];        /* level l >= 1 (level 0 ignored) */
+  int lo[COSMOS_FMR_MAX_LEVELS][3];            /* interior [lo, hi) of level l >= 1 */
+  int hi[COSMOS_FMR_MAX_LEVELS][3];
+} cosmos_fmr;
+
+/* Device workspace of the hierarchy calls: one RK4 workspace for the largest
+ * level, the four saved states (U_n and the three stage states) of every
+ * level that has a finer one, and the interpolation buffer.  0 if the
+ * hierarchy is invalid. */
+size_t cosmos_fmr_workspace_bytes(const cosmos_fmr* m, const cosmos_params* p);
+
+/* Initial data (cosmos_init_grid on every level, the gauge wave's wavelength
+ * being level 0's box), injection from the finest level down, then the ghost
+ * points of every level from its parent.  states[l]: level l's device state. */
+int cosmos_fmr_init(const cosmos_fmr* m, const cosmos_params* p, const cosmos_id* id, double* const* states,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/* One step of the hierarchy from time t: level l takes 2^l RK4 steps of
+ * dt0 / 2^l (Berger-Oliger order).  Asynchronous on `stream`.  Errors:
+ * COSMOS_EINVAL (hierarchy, NULL or repeated state, dt0 <= 0), COSMOS_EALIGN,
+ * COSMOS_EWORKSPACE, COSMOS_ECUDA. */
+int cosmos_fmr_step(const cosmos_fmr* m, const cosmos_params* p, double* const* states, double t, double dt0,
+                    void* ws, size_t ws_bytes, void* stream);
+
+/* Ghost points of level `level` (>= 1) of `child` from the parent state
+ * `parent` (spatial interpolation only); interior points are not touched. */
+int cosmos_fmr_prolong(const cosmos_fmr* m, const cosmos_params* p, int level, const double* parent, double* child,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Injection: the interior points of level `level` (>= 1) that lie on points of
+ * its parent overwrite those values of `parent`. */
+int cosmos_fmr_restrict(const cosmos_fmr* m, const cosmos_params* p, int level, const double* child, double* parent,
+                        void* stream);
+
 /* cosmos_constraints without a workspace argument, for callers that cannot
  * allocate device memory: code that runs while a stream is being captured
  * into a CUDA graph, inside host callbacks, or in a host application whose

@@ -48,6 +48,16 @@ class cosmos_batch_tuning(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int)]
 
 
+COSMOS_FMR_MAX_LEVELS = 8
+
+
+class cosmos_fmr(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("grid", cosmos_grid * COSMOS_FMR_MAX_LEVELS),
+                ("origin", (ctypes.c_int * 3) * COSMOS_FMR_MAX_LEVELS),
+                ("lo", (ctypes.c_int * 3) * COSMOS_FMR_MAX_LEVELS),
+                ("hi", (ctypes.c_int * 3) * COSMOS_FMR_MAX_LEVELS)]
+
+
 class CosmosError(RuntimeError):
     pass
 
@@ -57,6 +67,7 @@ _P = ctypes.c_void_p
 _G = ctypes.POINTER(cosmos_grid)
 _PP = ctypes.POINTER(cosmos_params)
 _IDP = ctypes.POINTER(cosmos_id)
+_FP = ctypes.POINTER(cosmos_fmr)
 _D = ctypes.c_double
 _S = ctypes.c_size_t
 
@@ -92,6 +103,11 @@ _SIGS = {
     "cosmos_batch_run": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
     "cosmos_batch_time_stage": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_batch_free": ([_P], None),
+    "cosmos_fmr_workspace_bytes": ([_FP, _PP], ctypes.c_size_t),
+    "cosmos_fmr_init": ([_FP, _PP, _IDP, ctypes.POINTER(ctypes.c_void_p), _P, _S, _P], ctypes.c_int),
+    "cosmos_fmr_step": ([_FP, _PP, ctypes.POINTER(ctypes.c_void_p), _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_fmr_prolong": ([_FP, _PP, ctypes.c_int, _P, _P, _P, _S, _P], ctypes.c_int),
+    "cosmos_fmr_restrict": ([_FP, _PP, ctypes.c_int, _P, _P, _P], ctypes.c_int),
     "cosmos_last_cuda_error": ([], ctypes.c_int),
     "cosmos_strerror": ([ctypes.c_int], ctypes.c_char_p),
 }
@@ -299,6 +315,37 @@ def cosmos_batch_free(plan) -> None:
     lib().cosmos_batch_free(plan)
 
 
+def _state_ptrs(states):
+    return (ctypes.c_void_p * len(states))(*[s.data_ptr() for s in states])
+
+
+def cosmos_fmr_workspace_bytes(m, p) -> int:
+    return lib().cosmos_fmr_workspace_bytes(ctypes.byref(m), ctypes.byref(p))
+
+
+def cosmos_fmr_init(m, p, ident, states, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_fmr_init(ctypes.byref(m), ctypes.byref(p), ctypes.byref(ident), _state_ptrs(states), w, nb,
+                                 _stream(stream))
+
+
+def cosmos_fmr_step(m, p, states, t, dt0, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_fmr_step(ctypes.byref(m), ctypes.byref(p), _state_ptrs(states), float(t), float(dt0), w, nb,
+                                 _stream(stream))
+
+
+def cosmos_fmr_prolong(m, p, level, parent, child, ws=None, stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_fmr_prolong(ctypes.byref(m), ctypes.byref(p), int(level), _ptr(parent), _ptr(child), w, nb,
+                                    _stream(stream))
+
+
+def cosmos_fmr_restrict(m, p, level, child, parent, stream=None) -> int:
+    return lib().cosmos_fmr_restrict(ctypes.byref(m), ctypes.byref(p), int(level), _ptr(child), _ptr(parent),
+                                     _stream(stream))
+
+
 # ---- convenience constructors (plain data) -----------------------------------
 def make_grid(n, h, x0=(0.0, 0.0, 0.0), pitch=None) -> cosmos_grid:
     nx, ny, nz = (n, n, n) if isinstance(n, int) else n
@@ -326,3 +373,22 @@ def make_id(kind, A=0.0, mu=0.0, sigma=0.125, q=(1.0, 1.0, 1.0), center=(0.0, 0.
     d.center[:] = list(center)
     d.a0, d.t = a0, t
     return d
+
+
+def make_fmr(levels, pitch_align=1) -> cosmos_fmr:
+    """cosmos_fmr from a list of per-level dicts (n, h, x0, origin, lo, hi), as
+    inputs.nested_boxes returns; rows padded to a multiple of pitch_align."""
+    if not 1 <= len(levels) <= COSMOS_FMR_MAX_LEVELS:
+        raise ValueError("1 to %d levels" % COSMOS_FMR_MAX_LEVELS)
+    m = cosmos_fmr()
+    m.levels = len(levels)
+    for l, lv in enumerate(levels):
+        nx = int(lv["n"][0])
+        pitch = -(-nx // pitch_align) * pitch_align
+        m.grid[l] = make_grid(tuple(int(v) for v in lv["n"]), tuple(float(v) for v in lv["h"]),
+                              tuple(float(v) for v in lv["x0"]), pitch=pitch)
+        for d in range(3):
+            m.origin[l][d] = int(lv["origin"][d])
+            m.lo[l][d] = int(lv["lo"][d])
+            m.hi[l][d] = int(lv["hi"][d])
+    return m

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "host.cuh"
 
 namespace cosmos {
 
@@ -15,6 +16,8 @@ static int cuda_fail(cudaError_t e) {
   g_last_cuda_error = (int)e;
   return COSMOS_ECUDA;
 }
+
+int cuda_error(cudaError_t e) { return cuda_fail(e); }
 
 #define CK(expr)                             \
   do {                                       \
@@ -74,7 +77,7 @@ static long n_blocks(const DevGrid& g) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int validate(const cosmos_grid* g, const cosmos_params* p) {
   if (!g || !p) return COSMOS_EINVAL;
@@ -91,12 +94,7 @@ int validate(const cosmos_grid* g, const cosmos_params* p) {
   return COSMOS_OK;
 }
 
-// Workspace sub-buffers (each 256-byte aligned), in doubles from ws.
-struct WsLayout {
-  size_t prim, flux, D, stageA, stageB, acc, hm, partial, final_, total_bytes;
-};
-
-static WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
+WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
   const DevGrid d = make_devgrid(g);
   const size_t fs = (size_t)d.fstride;
   const int nf = 24 + 4 * p->fluid + 2 * p->scalar;
@@ -168,6 +166,7 @@ struct InitArgs {
   int isc;  // index of phi (scalar on), else -1
   cosmos_id id;
   double H0;
+  double Lx;  // gauge-wave wavelength
 };
 
 __global__ void init_metric_kernel(const InitArgs a, double* __restrict__ U) {
@@ -182,7 +181,7 @@ __global__ void init_metric_kernel(const InitArgs a, double* __restrict__ U) {
   const double x[3] = {a.x0[0] + i * a.g.h[0], a.x0[1] + j * a.g.h[1], a.x0[2] + k * a.g.h[2]};
   if (a.id.kind == 0) {
     // gauge wave: gamma_xx = H, alpha = sqrt(H), K_xx = -d_t H / (2 sqrt(H))
-    const double Lx = a.g.nx * a.g.h[0];
+    const double Lx = a.Lx;
     const double ph = 2.0 * PI * (x[0] - a.id.t) / Lx;
     const double H = 1.0 - a.id.A * sin(ph);
     const double dtH = a.id.A * (2.0 * PI / Lx) * cos(ph);
@@ -285,10 +284,9 @@ static ConstraintLauncher constraint_launcher(const cosmos_params* p) {
 // pass; bit 2: algebra pass + combine.
 // f_lo, f_hi: field range of the derivative pass (f_hi = 0: all fields);
 // k_lo, k_cnt: plane range of the algebra pass (k_cnt = 0: all planes).
-static int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n,
-                     double* out, double* acc, double t_stage, double cdt, double bk, double* ws,
-                     const WsLayout& L, cudaStream_t s, int pass_mask = 7, int f_lo = 0, int f_hi = 0,
-                     int k_lo = 0, int k_cnt = 0) {
+int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n, double* out,
+              double* acc, double t_stage, double cdt, double bk, double* ws, const WsLayout& L, cudaStream_t s,
+              int pass_mask, int f_lo, int f_hi, int k_lo, int k_cnt) {
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.f_lo = f_lo;
@@ -326,11 +324,57 @@ static int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, con
   return COSMOS_OK;
 }
 
-static int check_ws(const WsLayout& L, void* ws, size_t ws_bytes) {
+int check_ws(const WsLayout& L, void* ws, size_t ws_bytes) {
   if (L.total_bytes == 0) return COSMOS_OK;
   if (!ws) return COSMOS_EINVAL;
   if (ws_bytes < L.total_bytes) return COSMOS_EWORKSPACE;
   if (((uintptr_t)ws & 255u) != 0) return COSMOS_EALIGN;
+  return COSMOS_OK;
+}
+
+int init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
+              size_t ws_bytes, cudaStream_t s, double Lx_wave) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!id || !state) return COSMOS_EINVAL;
+  if (!aligned16(state)) return COSMOS_EALIGN;
+  if (id->kind < 0 || id->kind > 2) return COSMOS_EINVAL;
+  if (id->kind == 0 && p->fluid) return COSMOS_EINVAL;                   // the gauge wave is vacuum
+  if (id->kind == 2 && (!p->fluid || !p->scalar)) return COSMOS_EINVAL;  // isocurvature: scalar + fluid
+  if (id->kind >= 1 && (!(id->sigma > 0.0) || !(id->a0 > 0.0) || !(id->q[0] > 0.0) || !(id->q[1] > 0.0) ||
+                        !(id->q[2] > 0.0)))
+    return COSMOS_EINVAL;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_INIT);
+  const bool need_ws = (id->kind >= 1 && p->fluid);
+  if (need_ws && (e = check_ws(L, ws, ws_bytes))) return e;
+  InitArgs a;
+  a.g = make_devgrid(g);
+  for (int d = 0; d < 3; ++d) a.x0[d] = g->x0[d];
+  a.nf = cosmos_nfields(p);
+  a.isc = p->scalar ? 24 + 4 * p->fluid : -1;
+  a.id = *id;
+  a.H0 = p->H0;
+  a.Lx = Lx_wave > 0.0 ? Lx_wave : g->nx * g->h[0];
+  init_metric_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a, state);
+  CK(cudaGetLastError());
+  if (need_ws) {
+    double* w = (double*)ws;
+    ConstraintArgs c;
+    memset(&c, 0, sizeof(c));
+    c.g = a.g;
+    c.c = make_coef(g, 0.0);
+    cosmos_params pv = *p;
+    pv.fluid = 0;
+    pv.scalar = 0;
+    c.ap = algebra_params(&pv, 0.0);
+    c.U = state;
+    c.hm = w + L.hm;
+    c.partial = w + L.partial;
+    CK(launch_constraints_vac(c, s));
+    init_tau_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a.g, make_coef(g, 0.0), id->kind == 2 ? a.isc : -1,
+                                                             w + L.hm, state);
+    CK(cudaGetLastError());
+  }
   return COSMOS_OK;
 }
 
@@ -357,48 +401,7 @@ size_t cosmos_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int 
 
 int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
                      size_t ws_bytes, void* stream) {
-  int e = validate(g, p);
-  if (e) return e;
-  if (!id || !state) return COSMOS_EINVAL;
-  if (!aligned16(state)) return COSMOS_EALIGN;
-  if (id->kind < 0 || id->kind > 2) return COSMOS_EINVAL;
-  if (id->kind == 0 && p->fluid) return COSMOS_EINVAL;                   // the gauge wave is vacuum
-  if (id->kind == 2 && (!p->fluid || !p->scalar)) return COSMOS_EINVAL;  // isocurvature: scalar + fluid
-  if (id->kind >= 1 && (!(id->sigma > 0.0) || !(id->a0 > 0.0) || !(id->q[0] > 0.0) || !(id->q[1] > 0.0) ||
-                        !(id->q[2] > 0.0)))
-    return COSMOS_EINVAL;
-  const WsLayout L = ws_layout(g, p, COSMOS_OP_INIT);
-  const bool need_ws = (id->kind >= 1 && p->fluid);
-  if (need_ws && (e = check_ws(L, ws, ws_bytes))) return e;
-  cudaStream_t s = (cudaStream_t)stream;
-  InitArgs a;
-  a.g = make_devgrid(g);
-  for (int d = 0; d < 3; ++d) a.x0[d] = g->x0[d];
-  a.nf = cosmos_nfields(p);
-  a.isc = p->scalar ? 24 + 4 * p->fluid : -1;
-  a.id = *id;
-  a.H0 = p->H0;
-  init_metric_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a, state);
-  CK(cudaGetLastError());
-  if (need_ws) {
-    double* w = (double*)ws;
-    ConstraintArgs c;
-    memset(&c, 0, sizeof(c));
-    c.g = a.g;
-    c.c = make_coef(g, 0.0);
-    cosmos_params pv = *p;
-    pv.fluid = 0;
-    pv.scalar = 0;
-    c.ap = algebra_params(&pv, 0.0);
-    c.U = state;
-    c.hm = w + L.hm;
-    c.partial = w + L.partial;
-    CK(launch_constraints_vac(c, s));
-    init_tau_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a.g, make_coef(g, 0.0), id->kind == 2 ? a.isc : -1,
-                                                             w + L.hm, state);
-    CK(cudaGetLastError());
-  }
-  return COSMOS_OK;
+  return init_grid(g, p, id, state, ws, ws_bytes, (cudaStream_t)stream, 0.0);
 }
 
 int cosmos_rhs(const cosmos_grid* g, const cosmos_params* p, const double* state, double* rhs, double t, void* ws,

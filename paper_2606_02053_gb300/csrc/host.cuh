@@ -1,0 +1,29 @@
+// Host-side helpers of the single-grid calls (api.cu) that other translation
+// units of libcosmos_gb300 build on (fmr.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace cosmos {
+
+// Workspace sub-buffers of the single-grid calls (each 256-byte aligned), in
+// doubles from the workspace pointer; total_bytes is the size the op needs.
+struct WsLayout {
+  size_t prim, flux, D, stageA, stageB, acc, hm, partial, final_, total_bytes;
+};
+WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op);
+int check_ws(const WsLayout& L, void* ws, size_t ws_bytes);  // COSMOS_OK, EINVAL, EWORKSPACE or EALIGN
+bool aligned16(const void* p);
+// One RK4 stage (or one of its passes) of one grid, as cosmos_rk4_stage runs it
+// (api.cu): pass_mask bit 0 fluid pre-pass, bit 1 derivative pass, bit 2
+// algebra pass + combine; f_lo/f_hi and k_lo/k_cnt restrict the passes.
+int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n, double* out,
+              double* acc, double t_stage, double cdt, double bk, double* ws, const WsLayout& L, cudaStream_t s,
+              int pass_mask = 7, int f_lo = 0, int f_hi = 0, int k_lo = 0, int k_cnt = 0);
+// cosmos_init_grid with the gauge wave's wavelength given (Lx_wave > 0) instead
+// of the grid's own length nx h_x.
+int init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
+              size_t ws_bytes, cudaStream_t s, double Lx_wave);
+int cuda_error(cudaError_t e);  // records e for cosmos_last_cuda_error; returns COSMOS_ECUDA
+
+}  // namespace cosmos

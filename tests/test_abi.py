@@ -85,3 +85,61 @@ def test_host_side_validation_without_gpu(libpath):
     assert C.lib().cosmos_rhs(ctypes.byref(bad), ctypes.byref(p), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
     pw = C.make_params(fluid=1, w=0.0)
     assert C.lib().cosmos_rhs(ctypes.byref(g), ctypes.byref(pw), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
+
+
+def test_fmr_struct_layout_matches_c(tmp_path):
+    from paper_2606_02053_gb300 import cosmos
+
+    src = tmp_path / "fsz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "cosmos.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(cosmos_fmr), offsetof(cosmos_fmr, grid),"
+        " offsetof(cosmos_fmr, origin), offsetof(cosmos_fmr, lo), offsetof(cosmos_fmr, hi));return 0;}\n")
+    exe = tmp_path / "fsz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
+    F = cosmos.cosmos_fmr
+    assert vals == [ctypes.sizeof(F), F.grid.offset, F.origin.offset, F.lo.offset, F.hi.offset]
+
+
+def test_fmr_hierarchy_validation_without_gpu(libpath):
+    """Hierarchy checks (spacing ratio, alignment, ghost width, nesting) run on
+    the host before anything is launched."""
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.inputs import nested_boxes
+
+    p = C.make_params(fluid=1, H0=40.0)
+    lv = nested_boxes(32, 1.0 / 32, (-0.5,) * 3, 3, [32, 32])
+    good = C.make_fmr(lv, 32)
+    nb = C.cosmos_fmr_workspace_bytes(good, p)
+    fs = [C.cosmos_field_stride(good.grid[l]) for l in range(3)]
+    assert nb >= 4 * 28 * (fs[0] + fs[1]) * 8  # saved states of levels 0 and 1
+    assert C.cosmos_fmr_workspace_bytes(C.make_fmr(lv[:1], 32), p) > 0  # a single level is a plain grid
+
+    def bad(edit):
+        m = C.make_fmr(lv, 32)
+        edit(m)
+        return m
+
+    cases = [
+        lambda m: setattr(m, "levels", 0),
+        lambda m: setattr(m, "levels", C.COSMOS_FMR_MAX_LEVELS + 1),
+        lambda m: m.lo[1].__setitem__(0, 2),                      # fewer than 3 ghost layers
+        lambda m: m.hi[2].__setitem__(1, 30),                     # 2 ghost layers above
+        lambda m: m.origin[1].__setitem__(2, 16),                 # x0 no longer matches the origin
+        lambda m: m.grid[2].h.__setitem__(0, 1.0 / 100),          # ratio not 2
+    ]
+    for edit in cases:
+        m = bad(edit)
+        assert C.cosmos_fmr_workspace_bytes(m, p) == 0
+        assert C.lib().cosmos_fmr_step(ctypes.byref(m), ctypes.byref(p), None, 0.0, 0.1, None, 0,
+                                       None) == C.COSMOS_EINVAL
+    # a level 2 whose interpolation would read level 1's ghost points
+    big = nested_boxes(32, 1.0 / 32, (-0.5,) * 3, 3, [32, 48])
+    assert C.cosmos_fmr_workspace_bytes(C.make_fmr(big, 32), p) == 0
+    # NULL states, short workspace
+    assert C.lib().cosmos_fmr_step(ctypes.byref(good), ctypes.byref(p), None, 0.0, 0.1, None, 0,
+                                   None) == C.COSMOS_EINVAL
+    states = (ctypes.c_void_p * 3)(256, 512, 768)
+    assert C.lib().cosmos_fmr_step(ctypes.byref(good), ctypes.byref(p), states, 0.0, 0.1, ctypes.c_void_p(256),
+                                   nb - 8, None) == C.COSMOS_EWORKSPACE
