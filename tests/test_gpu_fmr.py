@@ -155,3 +155,71 @@ def test_single_level_equals_rk4_step_bitwise(C, O):
     H.step(0.0, 0.25 / n, 3)
     ev.step(0.0, 0.25 / n, 3)
     assert torch.equal(ev.view()[..., :n], H.view(0)[..., :n])
+
+
+def test_bench_hierarchy_at_full_size(C, O):
+    """The bench's hierarchy (128^3 box + two nested 96^3 levels, FLRW + zeta,
+    fluid) after 4 hierarchy steps, through the same calls and launch shapes as
+    the bench, checked by what the oracle computes one by one: every ghost
+    point against the oracle's interpolation of the GPU's parent state
+    (interpolation tolerance), injection bitwise, the right-hand side at
+    sampled interior points of every level (RHS tolerance, plus the rounding
+    floor of the fluid's flux divergence, 64 eps max|tau~| / h; periodic index
+    wrap never reaches an interior stencil, so the oracle's grid function
+    applies),
+    and the symmetry of the data under x <-> y and x -> 2c - x on every level."""
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+    from paper_2606_02053_gb300.fmr import Hierarchy
+
+    n0, nc = 128, 96
+    h0 = 1.0 / n0
+    lv = inputs.nested_boxes(n0, h0, (-(n0 // 2) * h0,) * 3, 3, [nc, nc])
+    p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
+    H = Hierarchy(lv, p, pitch_align=32)
+    H.init(C.make_id(1, mu=0.5, sigma=0.125))
+    steps, dt0 = 4, 0.25 * h0
+    H.step(0.0, dt0, steps)
+    t = steps * dt0
+    S = [H.get(l) for l in range(3)]
+    op = oracle_params(O, p)
+    for l in (1, 2):
+        ref = O.fmr_prolong(lv, l, S[l - 1], S[l].copy())
+        assert field_errors(S[l], ref).max() <= INTERP_TOL, l
+        assert np.array_equal(O.fmr_restrict(lv, l, S[l], S[l - 1].copy()), S[l - 1]), l
+    rng = np.random.default_rng(71)
+    for l in range(3):
+        ev = Evolution(H.grid(l), p)
+        ev.state.copy_(H.states[l])
+        r = ev.get(ev.rhs(t))
+        del ev
+        lo, hi = lv[l]["lo"], lv[l]["hi"]
+        pts = np.stack([rng.integers(lo[d], hi[d], size=300) for d in range(3)], axis=1)
+        edge = [(lo[0], lo[1], lo[2]), (hi[0] - 1, hi[1] - 1, hi[2] - 1), (lo[0], hi[1] - 1, (lo[2] + hi[2]) // 2)]
+        pts = np.unique(np.concatenate([pts, np.array(edge)]), axis=0)
+        ref = O.rhs_points(O.level_grid(lv[l]), op, S[l], pts, t)
+        g = r[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+        err = np.abs(g - ref).max(axis=0)
+        bound = 1e-12 * np.maximum(np.abs(ref).max(axis=0), 1e-12 * np.abs(ref).max())
+        # The fluid fields' right-hand side is a difference of face fluxes of
+        # size ~ tau~ divided by h: its rounding floor is a few ulps of the flux
+        # over h, which early in the run exceeds 1e-12 of the momentum
+        # right-hand side itself (measured: 1.1e-11 against max 3.1 at h = 1/128).
+        eps = np.finfo(np.float64).eps
+        bound[24:28] += 64 * eps * np.abs(S[l][24]).max() / lv[l]["h"][0]
+        assert np.all(err <= bound), (l, np.argmax(err / bound), (err / bound).max())
+    perm = [0, 4, 2, 5, 1, 3, 6, 7, 11, 9, 12, 8, 10, 13, 15, 14, 16, 17, 19, 18, 20, 22, 21, 23, 24, 26, 25, 27]
+    sign = np.ones(28)
+    for f in (2, 3, 9, 10, 14, 18, 21, 25):  # odd under x -> -x
+        sign[f] = -1.0
+    for l in range(3):
+        s = S[l]
+        c = n0 // 2 if l == 0 else 47  # centre index of the level
+        scale = np.maximum(np.abs(s).reshape(28, -1).max(axis=1), 1e-8 * np.abs(s).max())
+        err_swap = np.abs(s.transpose(0, 1, 3, 2)[perm] - s).reshape(28, -1).max(axis=1) / scale
+        assert err_swap.max() <= 1e-10, (l, err_swap.max())
+        m = 2 * c + 1 if l else n0  # points mirrored about c inside the array (periodic on level 0)
+        part = s[..., :m]
+        refl = np.roll(part[..., ::-1], 2 * c + 1 - m, axis=3) if l == 0 else part[..., ::-1]
+        err_refl = np.abs(sign[:, None, None, None] * refl - part).reshape(28, -1).max(axis=1) / scale
+        assert err_refl.max() <= 1e-10, (l, err_refl.max())
