@@ -15,7 +15,7 @@ namespace cosmos {
 static size_t a256(size_t doubles) { return ((doubles * 8 + 255) & ~(size_t)255) / 8; }
 
 struct AdjLayout {
-  size_t U2, U3, U4, KB, KB2, LAM, Dfw, CB, prim, flux, vprim, FC, VF, CB10, total_bytes;
+  size_t U2, U3, U4, KB, KB2, LAM, Dfw, CB, prim, flux, vprim, FC, VF, CB10, limbs, expo, total_bytes;
 };
 
 static int nin_of(const cosmos_params* p) {
@@ -56,6 +56,11 @@ static AdjLayout adj_layout(const cosmos_grid* g, const cosmos_params* p, int op
   }
   if (op == COSMOS_OP_VJP) L.Dfw = take((size_t)nder(p->scalar) * fs);  // derivative pass of the linearisation point
   if (op == COSMOS_OP_ADJOINT || op == COSMOS_OP_VJP) {
+    // limb copy for the integer derivative pass (the forward stages and the
+    // linearisation points use the same derivative pass as cosmos_rk4_step)
+    const int nslot = 24 + 2 * p->scalar;
+    L.limbs = take((size_t)nslot * fs);
+    L.expo = take(((size_t)nslot + 1) / 2);
     L.CB = take(nin_of(p) * fs);
     if (p->fluid) {
       L.prim = take(4 * fs);
@@ -82,6 +87,15 @@ static int check_ws_adj(size_t need, void* ws, size_t ws_bytes) {
   if (ws_bytes < need) return COSMOS_EWORKSPACE;
   if ((uintptr_t)ws & 255u) return COSMOS_EALIGN;
   return COSMOS_OK;
+}
+
+// Limb copy of every derivative field of U for the integer derivative pass.
+static cudaError_t limbs_of(const cosmos_params* p, const DevGrid& g, const double* U, double* ws, const AdjLayout& L,
+                            StageArgs& a, cudaStream_t s) {
+  const int nslot = 24 + 2 * p->scalar;
+  a.L = (const long long*)(ws + L.limbs);
+  a.E = (const int*)(ws + L.expo);
+  return launch_limbs(g, U, p->fluid, 0, nslot, (int*)(ws + L.expo), (long long*)(ws + L.limbs), s);
 }
 
 static FluidParams fparams(double w) {
@@ -120,7 +134,8 @@ static cudaError_t vjp_once(const cosmos_grid* g, const cosmos_params* p, const 
   d.skip_ko = 1;
   a.D = d.D;
   {
-    const cudaError_t e = launch_stage_for(p, d, -1, s);
+    cudaError_t e = limbs_of(p, d.g, U, ws, L, d, s);
+    if (e == cudaSuccess) e = launch_stage_for(p, d, -1, s);
     if (e != cudaSuccess) return e;
   }
   if (p->fluid) {
@@ -168,6 +183,8 @@ static cudaError_t fwd_stage(const cosmos_grid* g, const cosmos_params* p, const
     a.prim = ws + L.prim;
     a.flux = ws + L.flux;
   }
+  const cudaError_t e = limbs_of(p, a.g, U_s, ws, L, a, s);
+  if (e != cudaSuccess) return e;
   return launch_stage_for(p, a, MODE_S1, s);
 }
 

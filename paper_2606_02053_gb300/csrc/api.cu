@@ -113,6 +113,11 @@ WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
       L.flux = take(12 * fs);
     }
     L.D = take((size_t)nder(p->scalar) * fs);
+    // limb copy of the stage state (8 bytes per value) for the integer
+    // derivative pass, one slot per field with derivatives, and their exponents
+    const int nslot = 24 + 2 * p->scalar;
+    L.limbs = take((size_t)nslot * fs);
+    L.expo = take(((size_t)nslot + 1) / 2);
     if (op == COSMOS_OP_RK4) {
       L.stageA = take(nf * fs);
       L.stageB = take(nf * fs);
@@ -313,6 +318,20 @@ int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const doub
     }
     a.prim = prim;
     a.flux = flux;
+  }
+  if (pass_mask & 2) {
+    // limb copy of the fields of this derivative pass (slots of fields f_lo .. f_hi - 1)
+    a.L = (const long long*)(ws + L.limbs);
+    a.E = (const int*)(ws + L.expo);
+    const int nf = cosmos_nfields(p), hi = f_hi > 0 ? f_hi : nf;
+    int s_lo = 1 << 30, s_hi = 0;
+    for (int f = f_lo; f < hi; ++f) {
+      if (p->fluid && f >= 24 && f < 28) continue;  // no derivatives of the fluid fields here
+      const int sl = (p->fluid && f >= 28) ? f - 4 : f;
+      s_lo = sl < s_lo ? sl : s_lo;
+      s_hi = sl + 1 > s_hi ? sl + 1 : s_hi;
+    }
+    CK(launch_limbs(a.g, U_s, p->fluid, s_lo, s_hi, (int*)(ws + L.expo), (long long*)(ws + L.limbs), s));
   }
   if ((pass_mask & 6) == 6) {
     CK(stage_launcher(p)(a, mode, s));

@@ -40,10 +40,13 @@ static long max_tiles(const cosmos_grid& g) {
 }
 
 struct BatchLayout {
-  std::vector<size_t> A, B, acc, prim, flux, D;  // per instance, in doubles from ws
-  size_t args, tiles, dtiles, kref;              // byte offsets
+  std::vector<size_t> A, B, acc, prim, flux, D, limbs;  // per instance, in doubles from ws
+  size_t args, tiles, dtiles, kref, expo;               // byte offsets (expo: n x nslot exponents)
   size_t total;
 };
+
+// limb slots of the integer derivative pass (stage_int.cuh)
+static int nslot_of(const cosmos_params* p) { return 24 + 2 * p->scalar; }
 
 // BX x DBY (32 x 8) tiles of every plane: the derivative pass's work list
 static long deriv_tiles(const cosmos_grid& g) {
@@ -68,6 +71,7 @@ static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_pa
     L.prim.push_back(p->fluid ? take(4 * fs * 8) / 8 : 0);
     L.flux.push_back(p->fluid ? take(12 * fs * 8) / 8 : 0);
     L.D.push_back(take((size_t)nder(p->scalar) * fs * 8) / 8);
+    L.limbs.push_back(take((size_t)nslot_of(p) * fs * 8) / 8);
     tiles += max_tiles(grids[i]);
     dtiles += deriv_tiles(grids[i]);
   }
@@ -75,6 +79,7 @@ static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_pa
   L.tiles = take(sizeof(BatchTile) * (size_t)tiles);
   L.dtiles = take(sizeof(BatchTile) * (size_t)dtiles);
   L.kref = take(sizeof(double) * (size_t)max_steps * 4 * n);
+  L.expo = take(sizeof(int) * (size_t)n * nslot_of(p));
   L.total = off;
   return L;
 }
@@ -216,6 +221,8 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
       a.cdt = cdt[s];
       a.bk = 2.0;
       a.D = wsd + L.D[i];
+      a.L = (const long long*)(wsd + L.limbs[i]);
+      a.E = (const int*)(b->ws + L.expo) + (size_t)i * nslot_of(p);
       if (p->fluid) {
         a.prim = wsd + L.prim[i];
         a.flux = wsd + L.flux[i];
@@ -271,6 +278,9 @@ int cosmos_batch_set_tuning(cosmos_batch b, const cosmos_batch_tuning* tuning) {
   return upload_tiles(b);
 }
 
+// persistent grid of the integer derivative pass: its resident blocks on every SM
+static int ideriv_blocks(cosmos_batch b) { return b->sms * COSMOS_IDERIV_MIN_BLOCKS; }
+
 static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStream_t s) {
   BatchStageLauncher launch = launch_batch_stage_vac;
   if (b->p.fluid && b->p.scalar)
@@ -288,8 +298,9 @@ static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStr
           launch_batch_fluid(args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
         return COSMOS_ECUDA;
       const double* kref = b->d_kref + ((size_t)st * 4 + stage) * b->n;
-      if (launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s, b->d_dtiles,
-                 b->ndtiles) != cudaSuccess)
+      if (launch_batch_limbs(args, b->n, nslot_of(&b->p), b->p.fluid, (int*)(b->ws + b->L.expo), s) != cudaSuccess ||
+          launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s, b->d_dtiles,
+                 b->ndtiles, ideriv_blocks(b)) != cudaSuccess)
         return COSMOS_ECUDA;
     }
   return COSMOS_OK;
@@ -338,8 +349,9 @@ int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stre
         launch_batch_fluid(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
       rc = COSMOS_ECUDA;
     if (rc == COSMOS_OK &&
-        launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s, b->d_dtiles,
-               b->ndtiles) != cudaSuccess)
+        (launch_batch_limbs(b->d_args, b->n, nslot_of(&b->p), b->p.fluid, (int*)(b->ws + b->L.expo), s) != cudaSuccess ||
+         launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s, b->d_dtiles,
+                b->ndtiles, ideriv_blocks(b)) != cudaSuccess))
       rc = COSMOS_ECUDA;
   }
   cudaEventRecord(e1, s);

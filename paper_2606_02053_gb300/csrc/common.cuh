@@ -98,6 +98,8 @@ struct StageArgs {
   int f_lo, f_hi;                  // derivative pass: only fields f_lo <= f < f_hi (f_hi = 0: all)
   int k_lo, k_cnt;                 // algebra pass: only planes k_lo .. k_lo + k_cnt - 1 (k_cnt = 0: all)
   int skip_ko;                     // derivative pass: leave the Kreiss-Oliger slots of D unwritten
+  const long long* __restrict__ L; // limb copy of U (stage_int.cuh); null: the FP64 derivative pass
+  const int* __restrict__ E;       // reference exponent of each limb slot
 };
 
 // Doubles per point of the derivative-pass buffer: first and second
@@ -121,6 +123,10 @@ struct ConstraintArgs {
   double* partial;   // [nblocks][8]: sum of squares (4) and max abs (4)
 };
 
+#ifndef COSMOS_IDERIV_MIN_BLOCKS
+#define COSMOS_IDERIV_MIN_BLOCKS 4  // integer derivative pass: resident blocks (of BX x DBY threads) per SM
+#endif
+
 // Launchers implemented per matter variant (stage_<variant>.cu).
 cudaError_t launch_stage_vac(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid(const StageArgs& a, int mode, cudaStream_t s);
@@ -129,15 +135,15 @@ cudaError_t launch_stage_fluid_scalar(const StageArgs& a, int mode, cudaStream_t
 // batched stage: derivative pass over the BX x DBY tile list (dtiles), algebra
 // pass over the tuned work list (tiles, mapping)
 typedef cudaError_t (*BatchStageLauncher)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
-                                          dim3, cudaStream_t, const BatchTile*, long);
+                                          dim3, cudaStream_t, const BatchTile*, long, int);
 cudaError_t launch_batch_stage_vac(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                   cudaStream_t, const BatchTile*, long);
+                                   cudaStream_t, const BatchTile*, long, int);
 cudaError_t launch_batch_stage_fluid(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                     cudaStream_t, const BatchTile*, long);
+                                     cudaStream_t, const BatchTile*, long, int);
 cudaError_t launch_batch_stage_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                      cudaStream_t, const BatchTile*, long);
+                                      cudaStream_t, const BatchTile*, long, int);
 cudaError_t launch_batch_stage_fluid_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
-                                            dim3, cudaStream_t, const BatchTile*, long);
+                                            dim3, cudaStream_t, const BatchTile*, long, int);
 cudaError_t launch_batch_fluid(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping, double w,
                                dim3 grid, dim3 block, cudaStream_t s);
 cudaError_t launch_constraints_vac(const ConstraintArgs& a, cudaStream_t s);
@@ -153,6 +159,14 @@ cudaError_t launch_vjp_scalar(const VjpArgs& a, cudaStream_t s);
 cudaError_t launch_vjp_fluid_scalar(const VjpArgs& a, cudaStream_t s);
 cudaError_t launch_init_zeta_vjp(const DevGrid& g, const Coef& c, const AlgebraParams& ap, const double* U,
                                  const double* lam, double* CB10, int fluid, double* zbar, cudaStream_t s);
+
+// limbs.cu: exponents of limb slots s_lo .. s_hi - 1 of U and its limb copy
+// (slot s = field s, or s + 4 past the fluid fields when the fluid is on)
+cudaError_t launch_limbs(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, int* E, long long* L,
+                         cudaStream_t s);
+// the same for every instance of a batch (args[i] = instance i's stage arguments;
+// E_all = the n x nslot exponents, contiguous, args[i].E = E_all + i nslot)
+cudaError_t launch_batch_limbs(const StageArgs* args, int n, int nslot, int fluid, int* E_all, cudaStream_t s);
 
 // fluid.cu
 cudaError_t launch_fluid_prim(const DevGrid& g, const double* U, double* prim, double w, cudaStream_t s);

@@ -1,0 +1,105 @@
+// Pre-pass of the integer derivative pass (stage_int.cuh): the reference
+// exponent of every limb slot, then the limb copy of the stage state.
+#include "stage_kernel.cuh"
+
+namespace cosmos {
+
+// E[s] = max over the grid of the biased exponent of slot s (E zeroed before).
+// Blocks stride over the rows (j, k); padding columns are never read.
+__global__ void field_exponent_kernel(const DevGrid g, const double* __restrict__ U, int s_lo, int fluid,
+                                      int* __restrict__ E) {
+  const int s = s_lo + blockIdx.y;
+  const double* F = U + (long)limb_field(s, fluid) * g.fstride;
+  unsigned m = 0;
+  const long rows = (long)g.ny * g.nz;
+  for (long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* R = F + r * g.pitch;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const unsigned e = (unsigned)(((unsigned long long)__double_as_longlong(__ldg(R + i)) >> 52) & 0x7FF);
+      m = e > m ? e : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned v = __shfl_down_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned*)E + s, m);
+}
+
+__global__ void to_limbs_kernel(const DevGrid g, const double* __restrict__ U, int s_lo, int fluid,
+                                const int* __restrict__ E, long long* __restrict__ L) {
+  const int s = s_lo + blockIdx.y;
+  const double* F = U + (long)limb_field(s, fluid) * g.fstride;
+  long long* Ls = L + (long)s * g.fstride;
+  const int e_ref = max(E[s], 1);
+  const long rows = (long)g.ny * g.nz;
+  for (long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const long o = r * g.pitch;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) Ls[o + i] = to_limbs(__ldg(F + o + i), e_ref);
+  }
+}
+
+// Batched pre-pass: blockIdx.z = instance, blockIdx.y = slot; the arguments
+// of instance i are args[i] (its stage input U, grid, limb copy and exponents).
+__global__ void batch_field_exponent_kernel(const StageArgs* __restrict__ args, int fluid) {
+  const StageArgs& a = args[blockIdx.z];
+  const DevGrid g = a.g;
+  const int s = blockIdx.y;
+  const double* F = a.U + (long)limb_field(s, fluid) * g.fstride;
+  unsigned m = 0;
+  const long rows = (long)g.ny * g.nz;
+  for (long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* R = F + r * g.pitch;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      const unsigned e = (unsigned)(((unsigned long long)__double_as_longlong(__ldg(R + i)) >> 52) & 0x7FF);
+      m = e > m ? e : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned v = __shfl_down_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned*)a.E + s, m);
+}
+
+__global__ void batch_to_limbs_kernel(const StageArgs* __restrict__ args, int fluid) {
+  const StageArgs& a = args[blockIdx.z];
+  const DevGrid g = a.g;
+  const int s = blockIdx.y;
+  const double* F = a.U + (long)limb_field(s, fluid) * g.fstride;
+  long long* Ls = const_cast<long long*>(a.L) + (long)s * g.fstride;
+  const int e_ref = max(a.E[s], 1);
+  const long rows = (long)g.ny * g.nz;
+  for (long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const long o = r * g.pitch;
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) Ls[o + i] = to_limbs(__ldg(F + o + i), e_ref);
+  }
+}
+
+cudaError_t launch_batch_limbs(const StageArgs* args, int n, int nslot, int fluid, int* E_all, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(E_all, 0, sizeof(int) * (size_t)n * nslot, s);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(32, (unsigned)nslot, (unsigned)n);
+  batch_field_exponent_kernel<<<grid, 128, 0, s>>>(args, fluid);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  batch_to_limbs_kernel<<<grid, 128, 0, s>>>(args, fluid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_limbs(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, int* E, long long* L,
+                         cudaStream_t s) {
+  if (s_hi <= s_lo) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(E + s_lo, 0, sizeof(int) * (s_hi - s_lo), s);
+  if (e != cudaSuccess) return e;
+  const long rows = (long)g.ny * g.nz;
+  const int threads = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64);
+  const dim3 grid((unsigned)(rows < 2048 ? rows : 2048), (unsigned)(s_hi - s_lo));
+  field_exponent_kernel<<<grid, threads, 0, s>>>(g, U, s_lo, fluid, E);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  to_limbs_kernel<<<grid, threads, 0, s>>>(g, U, s_lo, fluid, E, L);
+  return cudaGetLastError();
+}
+
+}  // namespace cosmos

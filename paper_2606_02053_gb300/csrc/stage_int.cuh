@@ -1,0 +1,290 @@
+// Derivative pass in exact integer arithmetic.
+//
+// GB300 runs FP64 at about 2 operations per clock per SM and 32-bit integer
+// adds and multiply-adds at about 60: the finite-difference and Kreiss-Oliger
+// stencils, integer-coefficient sums of neighbouring values, are cheaper in
+// integer arithmetic than in FP64, and can be made exact there.
+//
+// Representation ("limbs"): every value f of one field is held as the signed
+// 64-bit integer V = f 2^(1085 - e_ref), with e_ref the largest biased FP64
+// exponent of the field over the grid: the field's largest value has
+// 53 + 10 significant bits (|V| < 2^63), every value down to 2^-10 of it is
+// exact, and smaller ones are truncated by at most 2^-62 of the largest (a
+// relative 2e-15 even of a 256^3 second derivative of such a field, where the
+// tolerance is 1e-12).  On load V is split into three 21-bit digits
+// V = L0 + L1 2^21 + L2 2^42 (L0, L1 in [0, 2^21), L2 signed).  A stencil
+// sum_o c_o f_o with integer c_o is then the digit-wise sums sum_o c_o L_k(o):
+// with sum |c_o| <= 324 (the largest, the mixed derivative on staged first-
+// derivative sums) every digit sum stays below 2^31, so there are no carries
+// and the sum is exact.  Each result is rounded once to FP64 (round to
+// nearest even) and multiplied by its stencil coefficient (1/(12 h),
+// 1/(12 h^2), 1/(144 h_a h_b)): the stored value is within one rounding of the
+// exact stencil of the inputs.
+//
+// The state is converted to limbs by a pre-pass (limbs.cu: the exponent of
+// every field, then the conversion); the derivative pass reads the limb copy
+// (8 bytes per value, as the state) instead of the state and writes the same
+// derivative buffer as the FP64 pass.
+#pragma once
+
+#include "common.cuh"
+
+namespace cosmos {
+
+constexpr int LIMB_EXTRA = 10;                    // significant bits below the largest value's last place
+constexpr unsigned LIMB_MASK = (1u << 21) - 1;    // one 21-bit digit
+
+__device__ __forceinline__ int3 l_add(int3 a, int3 b) { return make_int3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ int3 l_sub(int3 a, int3 b) { return make_int3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ int3 l_mul(int3 a, int k) { return make_int3(a.x * k, a.y * k, a.z * k); }
+// a k + b
+__device__ __forceinline__ int3 l_mad(int3 a, int k, int3 b) { return make_int3(a.x * k + b.x, a.y * k + b.y, a.z * k + b.z); }
+
+// V of f for a field with reference exponent e_ref (>= the exponent of f).
+__device__ __forceinline__ long long to_limbs(double f, int e_ref) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(f);
+  const int e = (int)((b >> 52) & 0x7FF);
+  unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+  if (e) M |= 1ull << 52;
+  const int s = (e ? e : 1) - e_ref + LIMB_EXTRA;  // V = M 2^s, s <= 10
+  const unsigned long long V = s >= 0 ? M << s : (s > -64 ? M >> (-s) : 0ull);
+  return (b >> 63) ? -(long long)V : (long long)V;
+}
+
+// the digits of a stored V
+__device__ __forceinline__ int3 digits(long long V) {
+  return make_int3((int)(V & LIMB_MASK), (int)((V >> 21) & LIMB_MASK), (int)(V >> 42));
+}
+
+// FP64 (round to nearest even) of the unsigned 128-bit magnitude (uh, lo)
+// times 2^(e_ref - 1085), negated if neg.
+__device__ __forceinline__ double round_mag(unsigned long long uh, unsigned long long lo, bool neg, int e_ref) {
+  if ((uh | lo) == 0) return 0.0;
+  const int n = uh ? 127 - __clzll(uh) : 63 - __clzll(lo);  // leading one
+  int ex = n + e_ref - 1085 + 1023;                           // biased exponent of the result
+  unsigned long long m;
+  if (n <= 52) {
+    m = lo << (52 - n);
+  } else {
+    const int r = n - 52;  // bits dropped, < 64 (|value| < 2^73)
+    m = (lo >> r) | (r ? uh << (64 - r) : 0ull);
+    const int rb = r - 1;
+    const unsigned long long round = (lo >> rb) & 1ull;
+    const bool sticky = (lo & ((1ull << rb) - 1ull)) != 0;
+    if (round && (sticky || (m & 1ull))) {
+      ++m;
+      if (m >> 53) {
+        m >>= 1;
+        ++ex;
+      }
+    }
+  }
+  if (ex <= 0) return neg ? -0.0 : 0.0;  // below the normal range: far below any stencil of this field
+  unsigned long long bits = ((unsigned long long)ex << 52) | (m & 0xFFFFFFFFFFFFFull);
+  if (neg) bits |= 1ull << 63;
+  return __longlong_as_double((long long)bits);
+}
+
+// FP64 value of the digit sums S.x + S.y 2^21 + S.z 2^42 (|S.k| < 2^31) in the
+// units of a field with reference exponent e_ref.
+__device__ __forceinline__ double from_limbs(int3 S, int e_ref) {
+  if (e_ref >= 2047) return __longlong_as_double(0x7FF8000000000000ll);  // the field holds Inf or NaN
+  const long long t1 = (long long)S.x + ((long long)S.y << 21);         // |t1| < 2^52
+  if (S.z < (1 << 20) && S.z > -(1 << 20)) {                            // |value| < 2^63: one 64-bit word
+    const long long v = t1 + ((long long)S.z << 42);
+    const bool neg = v < 0;
+    return round_mag(0ull, neg ? (unsigned long long)(-v) : (unsigned long long)v, neg, e_ref);
+  }
+  // value = t1 + S.z 2^42 as a signed 128-bit integer (hi, lo)
+  const unsigned long long p = (unsigned long long)((long long)S.z << 42);
+  unsigned long long lo = p + (unsigned long long)t1;
+  long long hi = ((long long)S.z >> 22) + (t1 >> 63) + (lo < p ? 1 : 0);
+  const bool neg = hi < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0 ? 1 : 0);
+  }
+  return round_mag((unsigned long long)hi, lo, neg, e_ref);
+}
+
+// ---------------------------------------------------------------------------
+// Pre-pass.  Slot s of the limb copy holds field s, except that with the fluid
+// on the fields after the fluid ones (the scalar) move down by 4 (the fluid
+// fields have no derivatives in this pass).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int limb_field(int s, int fluid) { return (fluid && s >= 24) ? s + 4 : s; }
+
+// ---------------------------------------------------------------------------
+// Integer stencils (digit sums; the caller converts and scales)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int3 ldl(const long long* __restrict__ L, long o) { return digits(__ldg(L + o)); }
+
+__device__ __forceinline__ long limb_plane_off(const DevGrid& g, int x, int y, int k) {
+  return ((long)wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
+}
+
+// Digit sums of D_y (rows j0 .. j0+DBY-1) and D_z (rows j0-2 .. j0+DBY+1) on
+// the x-extended tile (halo 2), unscaled.
+__device__ __forceinline__ void stage_dydz_int(const DevGrid& g, const long long* __restrict__ Lf, int i0, int j0, int k,
+                                               int tid, int3* __restrict__ sDy, int3* __restrict__ sDz) {
+  constexpr int TXH = BX + 4;
+  for (int q = tid; q < TXH * DBY; q += BX * DBY) {
+    const int qx = q % TXH, qy = q / TXH;
+    const int x = i0 - 2 + qx, y = j0 + qy;
+    sDy[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off(g, x, y + 1, k)), ldl(Lf, limb_plane_off(g, x, y - 1, k))), 8),
+                   l_sub(ldl(Lf, limb_plane_off(g, x, y + 2, k)), ldl(Lf, limb_plane_off(g, x, y - 2, k))));
+  }
+  for (int q = tid; q < TXH * (DBY + 4); q += BX * DBY) {
+    const int qx = q % TXH, qy = q / TXH;
+    const int x = i0 - 2 + qx, y = j0 - 2 + qy;
+    sDz[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off(g, x, y, k + 1)), ldl(Lf, limb_plane_off(g, x, y, k - 1))), 8),
+                   l_sub(ldl(Lf, limb_plane_off(g, x, y, k + 2)), ldl(Lf, limb_plane_off(g, x, y, k - 2))));
+  }
+}
+
+// Neighbour sums of one axis at point n: D1 sum 8 (f+1 - f-1) - (f+2 - f-2)
+// and s_k = f(+k) + f(-k), k = 1, 2, 3 (each neighbour loaded once).
+template <int D>
+__device__ __forceinline__ void iaxis(const long long* __restrict__ L, const Nbr& n, int3& d1, int3& s1, int3& s2,
+                                      int3& s3) {
+  const int3 p1 = ldl(L, disp<D>(n, 1)), m1 = ldl(L, disp<D>(n, -1));
+  const int3 p2 = ldl(L, disp<D>(n, 2)), m2 = ldl(L, disp<D>(n, -2));
+  d1 = l_sub(l_mul(l_sub(p1, m1), 8), l_sub(p2, m2));
+  s1 = l_add(p1, m1);
+  s2 = l_add(p2, m2);
+  s3 = l_add(ldl(L, disp<D>(n, 3)), ldl(L, disp<D>(n, -3)));
+}
+
+// Field with first derivatives only: D1 along the three axes and the KO term.
+template <class T>
+__device__ __forceinline__ void ideriv_d1_point(const StageArgs& a, int m, const Nbr& n, bool ko_equal) {
+  const long fs = a.g.fstride;
+  const Coef& c = a.c;
+  double* __restrict__ D = a.D;
+  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+  const int f = T::d1_field(m);
+  const int s = ko_slot<T>(f);
+  const long long* Lf = a.L + (long)s * fs;
+  const int e = max(a.E[s], 1);
+  const int3 f0 = ldl(Lf, n.c);
+  int3 P1 = make_int3(0, 0, 0), P2 = P1, P3 = P1, d1, s1, s2, s3;
+  double ko = 0.0;
+#define COSMOS_IAXIS(AX)                                                                       \
+  iaxis<AX>(Lf, n, d1, s1, s2, s3);                                                            \
+  D[(long)(3 * m + AX) * fs + n.c] = from_limbs(d1, e) * c.d1b[AX];                            \
+  if (ko_equal) {                                                                              \
+    P1 = l_add(P1, s1);                                                                        \
+    P2 = l_add(P2, s2);                                                                        \
+    P3 = l_add(P3, s3);                                                                        \
+  } else {                                                                                     \
+    ko = fma(c.ko[AX], from_limbs(l_mad(f0, -20, l_mad(s2, -6, l_mad(s1, 15, s3))), e), ko);  \
+  }
+  COSMOS_IAXIS(0)
+  COSMOS_IAXIS(1)
+  COSMOS_IAXIS(2)
+#undef COSMOS_IAXIS
+  if (!a.skip_ko) {
+    if (ko_equal) ko = from_limbs(l_mad(f0, -60, l_mad(P2, -6, l_mad(P1, 15, P3))), e);  // scaled in the algebra pass
+    D[(long)(NDER0 + s) * fs + n.c] = ko;
+  }
+}
+
+// Everything the algebra needs from second-derivative field m2 at point n
+// (same outputs and layout as deriv_d2_point), each written as soon as it is
+// formed; D_y and D_z sums come from the staging area.
+template <class T>
+__device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, const Nbr& n, int tx, int ty,
+                                                bool ko_equal, const int3* __restrict__ sDy,
+                                                const int3* __restrict__ sDz) {
+  constexpr int TXH = BX + 4;
+  const long fs = a.g.fstride;
+  const Coef& c = a.c;
+  double* __restrict__ D = a.D;
+  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
+  const int f = T::d2_field(m2);
+  const int s = ko_slot<T>(f);
+  const long long* Lf = a.L + (long)s * fs;
+  const int e = max(a.E[s], 1);
+  const int m1 = T::d1_slot(f);
+  const long b = (long)(3 * T::ND1 + 6 * m2) * fs + n.c;
+  const int3 f0 = ldl(Lf, n.c);
+  const int3 f30 = l_mul(f0, -30);
+  int3 P1 = make_int3(0, 0, 0), P2 = P1, P3 = P1, d1, s1, s2, s3;
+  double ko = 0.0;
+  // second derivative 16 (f+1 + f-1) - (f+2 + f-2) - 30 f0 of axis AX into slot SL
+#define COSMOS_IAXIS2(AX, SL)                                                                  \
+  iaxis<AX>(Lf, n, d1, s1, s2, s3);                                                            \
+  D[b + SL * fs] = from_limbs(l_sub(l_mad(s1, 16, f30), s2), e) * c.d2b[AX];                   \
+  if (ko_equal) {                                                                              \
+    P1 = l_add(P1, s1);                                                                        \
+    P2 = l_add(P2, s2);                                                                        \
+    P3 = l_add(P3, s3);                                                                        \
+  } else {                                                                                     \
+    ko = fma(c.ko[AX], from_limbs(l_mad(f0, -20, l_mad(s2, -6, l_mad(s1, 15, s3))), e), ko);  \
+  }
+  COSMOS_IAXIS2(0, 0)
+  D[(long)(3 * m1 + 0) * fs + n.c] = from_limbs(d1, e) * c.d1b[0];
+  COSMOS_IAXIS2(1, 3)
+  COSMOS_IAXIS2(2, 5)
+#undef COSMOS_IAXIS2
+  if (!a.skip_ko) {
+    if (ko_equal) ko = from_limbs(l_mad(f0, -60, l_mad(P2, -6, l_mad(P1, 15, P3))), e);  // scaled in the algebra pass
+    D[(long)(NDER0 + s) * fs + n.c] = ko;
+  }
+  const int3* ry = sDy + ty * TXH + tx + 2;        // D_y sums at (i + o, j)
+  const int3* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z sums at (i + o, j), row stride TXH along y
+  D[(long)(3 * m1 + 1) * fs + n.c] = from_limbs(ry[0], e) * c.d1b[1];
+  D[(long)(3 * m1 + 2) * fs + n.c] = from_limbs(rz[0], e) * c.d1b[2];
+  D[b + 1 * fs] = from_limbs(l_sub(l_mul(l_sub(ry[1], ry[-1]), 8), l_sub(ry[2], ry[-2])), e) * c.mix[0];
+  D[b + 2 * fs] = from_limbs(l_sub(l_mul(l_sub(rz[1], rz[-1]), 8), l_sub(rz[2], rz[-2])), e) * c.mix[1];
+  D[b + 4 * fs] =
+      from_limbs(l_sub(l_mul(l_sub(rz[TXH], rz[-TXH]), 8), l_sub(rz[2 * TXH], rz[-2 * TXH])), e) * c.mix[2];
+}
+
+// One BX x DBY tile of one z-plane (block of BX x DBY threads), as deriv_tile
+// with the staging of one second-derivative field at a time.
+template <class T>
+__device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, int k, int3* __restrict__ sDy,
+                                            int3* __restrict__ sDz) {
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool valid = i < a.g.nx && j < a.g.ny;
+  const Nbr n = make_nbr(a.g, i, j, k);
+  const long fs = a.g.fstride;
+  const bool ko_equal = a.c.ko[0] == a.c.ko[1] && a.c.ko[1] == a.c.ko[2];
+  const int f_lo = a.f_lo, f_hi = a.f_hi > 0 ? a.f_hi : (1 << 30);
+#pragma unroll 1
+  for (int m = 0; m < T::ND1; ++m) {
+    const int f = T::d1_field(m);
+    if (T::d2_slot(f) >= 0 || f < f_lo || f >= f_hi) continue;
+    if (valid) ideriv_d1_point<T>(a, m, n, ko_equal);
+  }
+#pragma unroll 1
+  for (int m2 = 0; m2 < T::ND2; ++m2) {
+    const int f = T::d2_field(m2);
+    if (f < f_lo || f >= f_hi) continue;  // uniform across the block
+    stage_dydz_int(a.g, a.L + (long)ko_slot<T>(f) * fs, i0, j0, k, tid, sDy, sDz);
+    __syncthreads();
+    if (valid) ideriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy, sDz);
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS) ideriv_kernel(const StageArgs a) {
+  __shared__ int3 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
+  ideriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
+}
+
+// Persistent batched integer derivative pass over BX x DBY tiles of every instance.
+template <class T>
+__global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS)
+    batch_ideriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
+  __shared__ int3 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
+  for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
+    const BatchTile t = tiles[w];
+    ideriv_tile<T>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);
+  }
+}
+
+}  // namespace cosmos

@@ -334,6 +334,11 @@ __global__ void __launch_bounds__(BX* DBY* DBZ, COSMOS_DERIV_MIN_BLOCKS) deriv_k
   __shared__ double sDy[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NZ];
   deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z * DBZ, sDy, sDz);
 }
+}  // namespace cosmos
+
+#include "stage_int.cuh"
+
+namespace cosmos {
 
 // Inputs of the algebra pass at one point, read from global memory where the
 // generated code uses them (state values, then the derivative buffer, then the
@@ -540,7 +545,12 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   cudaError_t launch_stage_##NAME(const StageArgs& a, int mode, cudaStream_t s) {                               \
     dim3 grid = point_grid(a.g), block(BX, BY);                                                                \
     if (a.k_cnt > 0) grid.z = a.k_cnt;                                                                          \
-    if (mode < 0 || !(mode & 8)) deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY, DBZ), 0, s>>>(a);    \
+    if (mode < 0 || !(mode & 8)) {                                                                            \
+      if (a.L)                                                                                                  \
+        ideriv_kernel<T_##NAME><<<dim3(deriv_grid(a.g).x, deriv_grid(a.g).y, a.g.nz), dim3(BX, DBY), 0, s>>>(a); \
+      else                                                                                                      \
+        deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY, DBZ), 0, s>>>(a);                               \
+    }                                                                                                           \
     if (mode < 0) return cudaGetLastError();                                                                    \
     switch (mode & 7) {                                                                                             \
       case MODE_RHS: stage_kernel<T_##NAME, MODE_RHS><<<grid, block, 0, s>>>(a); break;                        \
@@ -552,8 +562,11 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   }                                                                                                             \
   cudaError_t launch_batch_stage_##NAME(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping,  \
                                         const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s,      \
-                                        const BatchTile* dtiles, long ndtiles) {                                  \
-    batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY, DBZ), 0, s>>>(args, dtiles, ndtiles);                    \
+                                        const BatchTile* dtiles, long ndtiles, int ideriv_blocks) {               \
+    if (ideriv_blocks > 0)                                                                                      \
+      batch_ideriv_kernel<T_##NAME><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);             \
+    else                                                                                                        \
+      batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY, DBZ), 0, s>>>(args, dtiles, ndtiles);                  \
     switch (mode) {                                                                                             \
       case MODE_S1:                                                                                             \
         batch_stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \
