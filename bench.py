@@ -39,14 +39,44 @@ BYTES_PER_POINT_STAGE = [8 * 3 * 24, 8 * 5 * 24, 8 * 5 * 24, 8 * 4 * 24]
 COMBINE_FLOPS = [2, 4, 4, 3]
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # each pass of the vacuum stage, from the committed ncu capture of the 96^3
-# case, and the hash of the kernel sources it was taken on.  Reported scaled to
-# the bench grid by points; null when the kernel sources differ from the
-# profiled ones.
-NCU_TRAFFIC = {"sources_sha256_16": "5b14bc71039dc68a", "grid": 96,
-               "bytes_per_launch": {"derivative": 254092288 + 1087588864, "algebra": 1376844288 + 802708480}}
+# case (the derivative pass: exponent scan + limb conversion + integer pass),
+# and the hash of the kernel sources it was taken on.  Reported scaled to the
+# bench grid by points; null when the kernel sources differ from the profiled
+# ones.
+NCU_TRAFFIC = {"sources_sha256_16": "1000771d94606900", "grid": 96,
+               "bytes_per_launch": {"derivative": (169890048 + 54016) + (169882880 + 122339072)
+                                    + (241765120 + 1106756000),
+                                    "algebra": 1377657000 + 800894208}}
 # derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
 DERIV_DOUBLES = 162
-KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_vac.cu", "generated/bssn_algebra.cuh"]
+KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_int.cuh", "limbs.cu", "stage_vac.cu",
+                  "generated/bssn_algebra.cuh"]
+
+
+def generated_algebra_ops(variant="vac"):
+    """Operation count of the generated pointwise algebra of a matter variant
+    (the expression DAG after common-subexpression elimination: every named
+    intermediate and every symmetric tensor component formed once), read from
+    the comment the code generator writes into the generated header."""
+    import ast
+    import re
+
+    path = os.path.join(ROOT, "paper_2606_02053_gb300", "csrc", "generated", "bssn_algebra.cuh")
+    with open(path) as fh:
+        for line in fh:
+            m = re.match(r"// variant (\w+): .* ops (\{.*\})", line)
+            if m and m.group(1) == variant:
+                return sum(ast.literal_eval(m.group(2)).values())
+    raise RuntimeError("no operation count for variant " + variant)
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def kernel_sources_hash():
@@ -642,31 +672,52 @@ def main():
     if cpu is not None:
         parts = cpu["flops_parts"]
         fl = lambda d: d["add"] + d["mul"] + d["div"] + d["sqrt"]  # noqa: E731
-        per_point = {"derivative": fl(parts["derivatives"]) + fl(parts["ko"]),
-                     "algebra": fl(parts["algebra"]) + statistics.mean(COMBINE_FLOPS) * STATE_FIELDS}
+        combine = statistics.mean(COMBINE_FLOPS) * STATE_FIELDS
+        # algebra pass: the generated algebra's operations + the KO multiply-add (2 per field) + the RK4
+        # combine; the oracle's count (its plain loops form every symmetric component twice) beside it
+        alg_flops = generated_algebra_ops("vac") + 2 * STATE_FIELDS + combine
+        oracle_flops = {"derivative": fl(parts["derivatives"]) + fl(parts["ko"]),
+                        "algebra": fl(parts["algebra"]) + combine}
         bytes_point = {"derivative": 8 * (STATE_FIELDS + DERIV_DOUBLES),
                        "algebra": 8 * (DERIV_DOUBLES + statistics.mean([b / 8 for b in BYTES_PER_POINT_STAGE]))}
         peak = fp64_peak / 1e12
+        hbm_peak, hbm_src = hbm_peak_gbs()
         traffic_ok = kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"]
 
-        def roofline(name):
-            achieved = pts * per_point[name] / avg[name] / 1e12
-            tr = None
-            if traffic_ok:
-                tr = NCU_TRAFFIC["bytes_per_launch"][name] * (n / NCU_TRAFFIC["grid"]) ** 3
-            return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": tr,
+        def traffic(name):
+            return NCU_TRAFFIC["bytes_per_launch"][name] * (n / NCU_TRAFFIC["grid"]) ** 3 if traffic_ok else None
+
+        def roof_algebra():
+            achieved = pts * alg_flops / avg["algebra"] / 1e12
+            return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": traffic("algebra"),
                     "traffic_note": "bytes per launch, ncu small-case capture scaled by points",
-                    "kernel": f"{name} pass ({'deriv_kernel' if name == 'derivative' else 'stage_kernel'}<T_vac>)",
-                    "avg_launch_ms": 1e3 * avg[name],
-                    "algorithmic_flops_per_point": per_point[name],
-                    "algorithmic_bytes_per_point": bytes_point[name],
-                    "hbm_GBps_algorithmic": pts * bytes_point[name] / avg[name] / 1e9,
+                    "kernel": "algebra pass (stage_kernel<T_vac>)", "avg_launch_ms": 1e3 * avg["algebra"],
+                    "algorithmic_flops_per_point": alg_flops,
+                    "flops_note": "generated algebra after CSE + KO multiply-add + RK4 combine",
+                    "oracle_flops_per_point": oracle_flops["algebra"],
+                    "algorithmic_bytes_per_point": bytes_point["algebra"],
+                    "hbm_GBps_algorithmic": pts * bytes_point["algebra"] / avg["algebra"] / 1e9,
                     "peak_source": "FP64 DFMA throughput measured in this run (cosmos_probe_fp64); nominal 1.25"}
 
+        def roof_derivative():
+            achieved = pts * bytes_point["derivative"] / avg["derivative"] / 1e9
+            return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": traffic("derivative"),
+                    "traffic_note": "bytes per launch (exponent scan + limb conversion + integer pass), ncu small-case "
+                                    "capture scaled by points",
+                    "kernel": "derivative pass (limb pre-pass + ideriv_kernel<T_vac>)",
+                    "avg_launch_ms": 1e3 * avg["derivative"],
+                    "algorithmic_bytes_per_point": bytes_point["derivative"],
+                    "stencil_flops_per_point_fp64_equivalent": oracle_flops["derivative"],
+                    "stencil_TFLOPs_fp64_equivalent": pts * oracle_flops["derivative"] / avg["derivative"] / 1e12,
+                    "arithmetic": "exact integer (fixed-point digits), not the FP64 pipe",
+                    "peak_source": "HBM copy bandwidth " + hbm_src}
+
+        rf = {"derivative": roof_derivative, "algebra": roof_algebra}
         dom = max(avg, key=avg.get)
         other = "algebra" if dom == "derivative" else "derivative"
-        roof, roof2 = roofline(dom), roofline(other)
+        roof, roof2 = rf[dom](), rf[other]()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -10,15 +10,20 @@ __global__ void field_exponent_kernel(const DevGrid g, const double* __restrict_
                                       int* __restrict__ E) {
   const int s = s_lo + blockIdx.y;
   const double* F = U + (long)limb_field(s, fluid) * g.fstride;
-  unsigned m = 0;
   const long rows = (long)g.ny * g.nz;
-  for (long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const double* R = F + r * g.pitch;
+  unsigned m = 0;
+  // four rows per iteration, so that four loads are in flight per thread
+  for (long r0 = 4 * (long)blockIdx.x; r0 < rows; r0 += 4 * (long)gridDim.x)
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
-      const unsigned e = (unsigned)(((unsigned long long)__double_as_longlong(__ldg(R + i)) >> 52) & 0x7FF);
-      m = e > m ? e : m;
+      unsigned long long b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = r0 + q < rows ? (unsigned long long)__double_as_longlong(__ldg(F + (r0 + q) * g.pitch + i)) : 0ull;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned e = (unsigned)((b[q] >> 52) & 0x7FF);
+        m = e > m ? e : m;
+      }
     }
-  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned v = __shfl_down_sync(0xffffffffu, m, o);

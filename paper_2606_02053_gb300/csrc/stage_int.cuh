@@ -117,10 +117,37 @@ __device__ __forceinline__ int limb_field(int s, int fluid) { return (fluid && s
 // ---------------------------------------------------------------------------
 // Integer stencils (digit sums; the caller converts and scales)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int3 ldl(const long long* __restrict__ L, long o) { return digits(__ldg(L + o)); }
+__device__ __forceinline__ int3 ldl(const long long* __restrict__ L, int o) { return digits(__ldg(L + o)); }
 
-__device__ __forceinline__ long limb_plane_off(const DevGrid& g, int x, int y, int k) {
-  return ((long)wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
+// Periodic neighbour offsets of one point within one field, as 32-bit
+// element offsets (a field of the grids this pass accepts has < 2^31 points).
+struct NbrI {
+  int x[7], y[7], z[7];
+  int c;
+};
+
+__device__ __forceinline__ NbrI make_nbri(const DevGrid& g, int i, int j, int k) {
+  NbrI n;
+  const int row = g.pitch, plane = g.pitch * g.ny;
+#pragma unroll
+  for (int o = -3; o <= 3; ++o) {
+    n.x[o + 3] = wrap_index(i + o, g.nx);
+    n.y[o + 3] = wrap_index(j + o, g.ny) * row;
+    n.z[o + 3] = wrap_index(k + o, g.nz) * plane;
+  }
+  n.c = n.z[3] + n.y[3] + n.x[3];
+  return n;
+}
+
+template <int D>
+__device__ __forceinline__ int dispi(const NbrI& n, int o) {
+  if (D == 0) return n.z[3] + n.y[3] + n.x[o + 3];
+  if (D == 1) return n.z[3] + n.y[o + 3] + n.x[3];
+  return n.z[o + 3] + n.y[3] + n.x[3];
+}
+
+__device__ __forceinline__ int limb_plane_off(const DevGrid& g, int x, int y, int k) {
+  return (wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
 }
 
 // Digit sums of D_y (rows j0 .. j0+DBY-1) and D_z (rows j0-2 .. j0+DBY+1) on
@@ -145,19 +172,19 @@ __device__ __forceinline__ void stage_dydz_int(const DevGrid& g, const long long
 // Neighbour sums of one axis at point n: D1 sum 8 (f+1 - f-1) - (f+2 - f-2)
 // and s_k = f(+k) + f(-k), k = 1, 2, 3 (each neighbour loaded once).
 template <int D>
-__device__ __forceinline__ void iaxis(const long long* __restrict__ L, const Nbr& n, int3& d1, int3& s1, int3& s2,
+__device__ __forceinline__ void iaxis(const long long* __restrict__ L, const NbrI& n, int3& d1, int3& s1, int3& s2,
                                       int3& s3) {
-  const int3 p1 = ldl(L, disp<D>(n, 1)), m1 = ldl(L, disp<D>(n, -1));
-  const int3 p2 = ldl(L, disp<D>(n, 2)), m2 = ldl(L, disp<D>(n, -2));
+  const int3 p1 = ldl(L, dispi<D>(n, 1)), m1 = ldl(L, dispi<D>(n, -1));
+  const int3 p2 = ldl(L, dispi<D>(n, 2)), m2 = ldl(L, dispi<D>(n, -2));
   d1 = l_sub(l_mul(l_sub(p1, m1), 8), l_sub(p2, m2));
   s1 = l_add(p1, m1);
   s2 = l_add(p2, m2);
-  s3 = l_add(ldl(L, disp<D>(n, 3)), ldl(L, disp<D>(n, -3)));
+  s3 = l_add(ldl(L, dispi<D>(n, 3)), ldl(L, dispi<D>(n, -3)));
 }
 
 // Field with first derivatives only: D1 along the three axes and the KO term.
 template <class T>
-__device__ __forceinline__ void ideriv_d1_point(const StageArgs& a, int m, const Nbr& n, bool ko_equal) {
+__device__ __forceinline__ void ideriv_d1_point(const StageArgs& a, int m, const NbrI& n, bool ko_equal) {
   const long fs = a.g.fstride;
   const Coef& c = a.c;
   double* __restrict__ D = a.D;
@@ -193,7 +220,7 @@ __device__ __forceinline__ void ideriv_d1_point(const StageArgs& a, int m, const
 // (same outputs and layout as deriv_d2_point), each written as soon as it is
 // formed; D_y and D_z sums come from the staging area.
 template <class T>
-__device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, const Nbr& n, int tx, int ty,
+__device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, const NbrI& n, int tx, int ty,
                                                 bool ko_equal, const int3* __restrict__ sDy,
                                                 const int3* __restrict__ sDz) {
   constexpr int TXH = BX + 4;
@@ -249,7 +276,7 @@ __device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int i = i0 + tx, j = j0 + ty;
   const bool valid = i < a.g.nx && j < a.g.ny;
-  const Nbr n = make_nbr(a.g, i, j, k);
+  const NbrI n = make_nbri(a.g, i, j, k);
   const long fs = a.g.fstride;
   const bool ko_equal = a.c.ko[0] == a.c.ko[1] && a.c.ko[1] == a.c.ko[2];
   const int f_lo = a.f_lo, f_hi = a.f_hi > 0 ? a.f_hi : (1 << 30);
