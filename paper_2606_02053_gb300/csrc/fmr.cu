@@ -428,16 +428,20 @@ int advance(const Ctx& c, int l, double t, double dt, double theta0) {
   double* Y3 = child ? c.saved(l, 2) : w + W.stageB;
   double* Y4 = child ? c.saved(l, 3) : w + W.stageA;
   const double dt2 = 0.5 * dt;
+  // on a refined level the algebra pass skips the ghost z-planes: whatever it
+  // would write there is replaced from the parent before it is read
+  const int k_lo = v.lo[2], k_cnt = v.hi[2] - v.lo[2];
   int e;
   if (l > 0 && (e = fill_stage(c, l, theta0, 1, U))) return e;
   if (child) FCK(cudaMemcpyAsync(c.saved(l, 0), U, c.H.nf * v.fs * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-  if ((e = run_stage(g, c.p, MODE_S1, U, U, Y2, acc, t, dt2, 2.0, w, W, c.s))) return e;
+  if ((e = run_stage(g, c.p, MODE_S1, U, U, Y2, acc, t, dt2, 2.0, w, W, c.s, 7, 0, 0, k_lo, k_cnt))) return e;
   if (l > 0 && (e = fill_stage(c, l, theta0, 2, Y2))) return e;
-  if ((e = run_stage(g, c.p, MODE_S23, Y2, U, Y3, acc, t + dt2, dt2, 2.0, w, W, c.s))) return e;
+  if ((e = run_stage(g, c.p, MODE_S23, Y2, U, Y3, acc, t + dt2, dt2, 2.0, w, W, c.s, 7, 0, 0, k_lo, k_cnt))) return e;
   if (l > 0 && (e = fill_stage(c, l, theta0, 3, Y3))) return e;
-  if ((e = run_stage(g, c.p, MODE_S23, Y3, U, Y4, acc, t + dt2, dt, 2.0, w, W, c.s))) return e;
+  if ((e = run_stage(g, c.p, MODE_S23, Y3, U, Y4, acc, t + dt2, dt, 2.0, w, W, c.s, 7, 0, 0, k_lo, k_cnt))) return e;
   if (l > 0 && (e = fill_stage(c, l, theta0, 4, Y4))) return e;
-  if ((e = run_stage(g, c.p, MODE_S4, Y4, U, nullptr, acc, t + dt, dt / 6.0, 2.0, w, W, c.s))) return e;
+  if ((e = run_stage(g, c.p, MODE_S4, Y4, U, nullptr, acc, t + dt, dt / 6.0, 2.0, w, W, c.s, 7, 0, 0, k_lo, k_cnt)))
+    return e;
   if (child) {
     if ((e = advance(c, l + 1, t, dt2, 0.0))) return e;
     if ((e = advance(c, l + 1, t + dt2, dt2, 0.5))) return e;
