@@ -1,9 +1,13 @@
-// BSSN right-hand side + RK4 stage, as two passes per stage (FP64 throughout):
+// BSSN right-hand side + RK4 stage, as two passes per stage:
 //
-//  * derivative pass (deriv_kernel, batch_deriv_kernel): for one BX x DBY tile
-//    of a z-plane, every 4th-order centred first and second derivative the
-//    algebra needs and the 6th-derivative Kreiss-Oliger term of every
-//    non-fluid field, written to the derivative buffer D;
+//  * derivative pass: for one BX x DBY tile of a z-plane, every 4th-order
+//    centred first and second derivative the algebra needs and the
+//    6th-derivative Kreiss-Oliger term of every non-fluid field, written to
+//    the derivative buffer D.  The launchers run it in exact integer
+//    arithmetic on a fixed-point copy of the state (stage_int.cuh:
+//    ideriv_kernel, batch_ideriv_kernel) whenever the arguments carry that
+//    copy, which every path of the library does; deriv_kernel and
+//    batch_deriv_kernel below are the same stencils in FP64;
 //  * algebra pass (stage_kernel, batch_stage_kernel): one point per thread,
 //    the generated pointwise BSSN + matter algebra on the state and D, the KO
 //    term or the Kurganov-Tadmor flux divergence, and the RK4 stage combine.
