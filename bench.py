@@ -106,11 +106,13 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "scan", "adjoint", "flrw", "fmr"],
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "scan", "adjoint", "flrw", "fmr", "isocurvature", "mode"],
                     help="sweep: single 256^3 grid (headline); scan: 64-instance batched threshold scan; "
                          "adjoint: gradients of collapse diagnostics at 96^3; flrw: 128^3 FLRW + zeta, "
                          "200 steps, constraint norms; fmr: 128^3 FLRW + zeta with two nested 96^3 "
-                         "refinement levels")
+                         "refinement levels; isocurvature: 128^3 fluid + scalar isocurvature data; mode: "
+                         "128^3 single-mode FLRW perturbation")
     ap.add_argument("--adjoint-steps", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-grid", type=int, default=96, help=argparse.SUPPRESS)
     ap.add_argument("--instances", type=int, default=64, help=argparse.SUPPRESS)
@@ -142,9 +144,15 @@ def flrw_workload(args):
     dt = 0.25 * h
     ev.init(ident)
     ev.step(0.0, dt, steps=max(args.warmup, 1))  # warm-up, then restart from the initial data
-    ev.init(ident)
     stream = torch.cuda.current_stream()
-    norms = [(0, ev.constraints()[1].tolist())]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev.init(ident)
+    torch.cuda.synchronize()
+    init_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    norms = [(0, ev.constraints()[1].tolist())]  # synchronous: the norms come back to the host
+    constraints_ms = 1e3 * (time.perf_counter() - t0)
     total_ms = 0.0
     for s0 in range(0, steps, every):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -164,7 +172,102 @@ def flrw_workload(args):
             "constraint_norms": {"columns": ["step", "L2_H", "L2_Mx", "L2_My", "L2_Mz", "Linf_H", "Linf_Mx",
                                              "Linf_My", "Linf_Mz"],
                                  "rows": [[s] + v for s, v in norms]},
-            "gpu_launches": steps * 4 * 4}  # per stage: primitives, face fluxes, derivative, algebra passes
+            "initial_data_ms": init_ms, "constraints_ms_per_evaluation": constraints_ms,
+            "gpu_launches": steps * 4 * 6}  # per stage: primitives, fluxes, exponents, limbs, derivative, algebra
+    print(json.dumps(line), flush=True)
+
+
+def isocurvature_workload(args):
+    """128^3 FLRW + zeta with a massless-scalar isocurvature profile (initial-data
+    kind 2: phi = A exp(-r^2/(2 sigma^2)), A = 0.02, the fluid energy from the
+    discrete Hamiltonian constraint with both sources), fluid + scalar, 100 RK4
+    steps of dt = h/4: throughput and the constraint norms at the start and the end."""
+    import torch
+
+    from paper_2606_02053_gb300 import build
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    build.build()
+    n, steps = 128, 100
+    h = 1.0 / n
+    p = C.make_params(slicing=0, shift=1, fluid=1, scalar=1, w=1.0 / 3.0, H0=40.0)
+    ev = Evolution(C.make_grid(n, h, x0=(-(n // 2) * h,) * 3), p)
+    ident = C.make_id(2, A=0.02, mu=0.3, sigma=0.125, q=(1.0, 0.9, 1.1))
+    dt = 0.25 * h
+    ev.init(ident)
+    ev.step(0.0, dt, steps=max(args.warmup, 1))
+    ev.init(ident)
+    norms0 = ev.constraints()[1].tolist()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ev.step(0.0, dt, steps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    norms1 = ev.constraints()[1].tolist()
+    line = {"metric": "FP64 grid-point RK4 updates/sec, 128^3 isocurvature data (fluid + scalar)",
+            "value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": max(args.warmup, 1), "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "isocurvature_128^3_fluid_scalar", "grid": n, "A": 0.02, "mu": 0.3,
+                       "sigma": 0.125, "q": [1.0, 0.9, 1.1], "H0L": 40.0, "dt_over_h": 0.25},
+            "constraint_norms": {"columns": ["L2_H", "L2_Mx", "L2_My", "L2_Mz", "Linf_H", "Linf_Mx", "Linf_My",
+                                             "Linf_Mz"], "start": norms0, "end": norms1},
+            "gpu_launches": steps * 4 * 6}
+    print(json.dumps(line), flush=True)
+
+
+def mode_workload(args):
+    """The paper's first example on a 128^3 grid: radiation FLRW (w = 1/3, H0 = 2)
+    with the lapse perturbed by one Fourier mode along x, alpha = 1 + 1e-7 cos(2 pi x),
+    harmonic slicing with the background trace and a frozen shift, no
+    Kreiss-Oliger term, evolved to t = 0.5 (256 steps of dt = h/4): throughput
+    and the complex amplitude of the mode in K at the end (the linear-theory
+    comparison is the test suite's)."""
+    import numpy as np
+    import torch
+
+    from paper_2606_02053_gb300 import build
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    build.build()
+    n, H0, eps, w = 128, 2.0, 1e-7, 1.0 / 3.0
+    h = 1.0 / n
+    steps = int(round(0.5 / (0.25 * h)))
+    p = C.make_params(slicing=1, shift=0, ko_sigma=0.0, fluid=1, w=w, H0=H0)
+    ev = Evolution(C.make_grid(n, h), p)
+    x = h * np.arange(n)
+    s = np.zeros((28, n, n, n))
+    s[0] = s[1] = s[4] = s[6] = 1.0
+    s[7] = -3.0 * H0
+    s[17] = (1.0 + eps * np.cos(2.0 * np.pi * x))[None, None, :]
+    s[24] = 3.0 * H0 * H0 / (8.0 * np.pi)
+    dt = 0.25 * h
+    ev.set_state(s)
+    ev.step(0.0, dt, steps=max(args.warmup, 1))
+    ev.set_state(s)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ev.step(0.0, dt, steps=steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    K = ev.view()[7, :, :, :n].mean(dim=(0, 1)).cpu().numpy()
+    amp = complex(K @ (np.exp(-2j * np.pi * x) * (2.0 / n)))
+    line = {"metric": "FP64 grid-point RK4 updates/sec, 128^3 single-mode FLRW perturbation",
+            "value": n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": max(args.warmup, 1), "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "single_mode_128^3_radiation_fluid", "grid": n, "eps": eps, "H0": H0,
+                       "t_end": steps * dt, "dt_over_h": 0.25, "slicing": "harmonic", "shift": "frozen"},
+            "K_mode_amplitude_end": [amp.real, amp.imag],
+            "gpu_launches": steps * 4 * 6}
     print(json.dumps(line), flush=True)
 
 
@@ -236,7 +339,7 @@ def fmr_workload(args):
     ms_plain = e0.elapsed_time(e1)
     del evs
     value = interior * args.steps / (ms * 1e-3)
-    launches_per_level_step = 16  # 4 stages x (primitives, face fluxes, derivative, algebra)
+    launches_per_level_step = 24  # 4 stages x (primitives, fluxes, exponents, limbs, derivative, algebra)
     launches_per_fill = 4         # time interpolation, x, y and z passes
     launches = sum(2 ** l * (launches_per_level_step + (4 * launches_per_fill if l else 0)) for l in range(nlev))
     launches += sum(2 ** (l - 1) for l in range(1, nlev))  # injections
@@ -340,7 +443,7 @@ def scan_workload(args):
                        "points_total": int(total_pts), "grid_sizes": [d["n"] for d in inst_all]},
             "per_instance_loop_value": total_pts * K / t_loop, "batched_speedup": t_loop / t_batch,
             "batched_vs_loop_max_abs_diff": max_diff, "autotune": tune,
-            "gpu_launches": K * 4 * 4}  # per stage: primitives, face fluxes, derivative, algebra passes
+            "gpu_launches": K * 4 * 6}  # per stage: primitives, fluxes, exponents, limbs, derivative, algebra
     print(json.dumps(line), flush=True)
 
 
@@ -549,6 +652,10 @@ def main():
         return flrw_workload(args)
     if args.workload == "fmr":
         return fmr_workload(args)
+    if args.workload == "isocurvature":
+        return isocurvature_workload(args)
+    if args.workload == "mode":
+        return mode_workload(args)
 
     import numpy as np
     import torch
@@ -623,7 +730,7 @@ def main():
     nranks = ws_
     pts = float(n) ** 3
     value = nranks * pts * args.steps / elapsed
-    gpu_launches = 8 * args.steps  # per stage: derivative kernel + algebra kernel
+    gpu_launches = 16 * args.steps  # per stage: exponent scan, limb copy, integer derivative pass, algebra pass
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     nbytes = ev.state.numel() * 8
