@@ -778,7 +778,7 @@ def main():
     avg = {name: statistics.mean([x for st in pass_ms[q] for x in st]) * 1e-3
            for q, name in enumerate(["derivative", "algebra"])}
     stage_avg = [statistics.mean(pass_ms[0][s]) + statistics.mean(pass_ms[1][s]) for s in range(4)]
-    roof, roof2 = None, None
+    roof, roof2, sweep = None, None, None
     if cpu is not None:
         parts = cpu["flops_parts"]
         fl = lambda d: d["add"] + d["mul"] + d["div"] + d["sqrt"]  # noqa: E731
@@ -828,13 +828,26 @@ def main():
         dom = max(avg, key=avg.get)
         other = "algebra" if dom == "derivative" else "derivative"
         roof, roof2 = rf[dom](), rf[other]()
+        # the whole sweep against the slower of the FP64 rate and HBM at peak, on the algorithmic work of
+        # both passes; the stencils count as the FP64 flops they stand for although integer units do them
+        f_pt = alg_flops + oracle_flops["derivative"]
+        b_pt = bytes_point["derivative"] + bytes_point["algebra"]
+        t_f = 4 * pts * f_pt / (peak * 1e12)
+        t_b = 4 * pts * b_pt / (hbm_peak * 1e9)
+        sweep = {"bound": "alu" if t_f >= t_b else "hbm", "flops_per_point_stage": f_pt,
+                 "bytes_per_point_stage": b_pt, "roofline_ms_per_step": 1e3 * max(t_f, t_b),
+                 "fp64_ms_per_step": 1e3 * t_f, "hbm_ms_per_step": 1e3 * t_b,
+                 "ms_per_step": 1e3 * elapsed / args.steps,
+                 "frac": max(t_f, t_b) / (elapsed / args.steps),
+                 "note": "roofline time / measured time for a whole RK4 step (both passes, all 4 stages)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": n, "fields": STATE_FIELDS, "dt_over_h": 0.25,
                        "parallelism": f"replicas{nranks}" if nranks > 1 else "single",
                        "l2": "inputs larger than L2 (3.2 GB state per level)"},
-            "stage_ms": stage_avg, "roofline": roof, "roofline_other_kernel": roof2, "gpu_launches": gpu_launches,
+            "stage_ms": stage_avg, "roofline": roof, "roofline_other_kernel": roof2, "roofline_sweep": sweep,
+            "gpu_launches": gpu_launches,
             "e2e": e2e, "clocks": clk,
             "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"],
                                                       "kind": "oracle", "sample": cpu["sample"],

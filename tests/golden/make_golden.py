@@ -56,10 +56,13 @@ def case_values(n, params, idd, dt):
     rng = np.random.default_rng(SEED)
     pts = np.stack([rng.integers(0, n[a], N_SAMPLES) for a in range(3)], axis=1)  # (i, j, k)
     flat = (pts[:, 2] * n[1] + pts[:, 1]) * n[0] + pts[:, 0]
-    r = O.rhs(g, P, s, 0.0).reshape(s.shape[0], -1)[:, flat]
-    u1 = O.rk4_step(g, P, s.copy(), 0.0, dt).reshape(s.shape[0], -1)[:, flat]
+    r = O.rhs(g, P, s, 0.0).reshape(s.shape[0], -1)
+    u1 = O.rk4_step(g, P, s.copy(), 0.0, dt).reshape(s.shape[0], -1)
     ham_mom, norms = O.constraints(g, P, s)
-    return {"points_ijk": pts.tolist(), "rhs": hexes(r), "rk4_step": hexes(u1), "norms": hexes(norms)}
+    # each field's largest magnitude over the whole grid: the scale the parity tolerances refer to
+    return {"points_ijk": pts.tolist(), "rhs": hexes(r[:, flat]), "rk4_step": hexes(u1[:, flat]),
+            "rhs_field_max": hexes(np.abs(r).max(axis=1)), "rk4_step_field_max": hexes(np.abs(u1).max(axis=1)),
+            "norms": hexes(norms)}
 
 
 def main():
