@@ -24,6 +24,9 @@
  *      then (fluid on) 24 tau~ = sqrt(gamma) E, 25..27 S~_i = sqrt(gamma) J_i,
  *      then (scalar on) phi, Pi  (Pi = -n^mu d_mu phi).
  *    Padding columns i in [nx, pitch) are never read or written.
+ *    Limits: nz <= 65535, ceil(ny / 4) <= 65535 and fstride < 2^31 (one
+ *    field's element offsets fit in 32 bits; a state of 24 such fields
+ *    would exceed the device memory anyway); else COSMOS_EINVAL.
  *  - Memory: every pointer named state/rhs/ws/... is DEVICE memory owned by
  *    the caller (e.g. a torch CUDA tensor), 16-byte aligned.  The library
  *    allocates no device memory in any call.  Work buffers are passed as

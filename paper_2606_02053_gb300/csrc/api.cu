@@ -83,6 +83,8 @@ int validate(const cosmos_grid* g, const cosmos_params* p) {
   if (!g || !p) return COSMOS_EINVAL;
   if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->pitch < g->nx) return COSMOS_EINVAL;
   if (g->nz > 65535 || (g->ny + BY - 1) / BY > 65535) return COSMOS_EINVAL;
+  // the derivative pass forms neighbour offsets within one field in 32 bits
+  if ((long long)g->pitch * g->ny * g->nz >= (1ll << 31)) return COSMOS_EINVAL;
   for (int d = 0; d < 3; ++d)
     if (!(g->h[d] > 0.0) || !isfinite(g->h[d])) return COSMOS_EINVAL;
   if (p->slicing != 0 && p->slicing != 1) return COSMOS_EINVAL;

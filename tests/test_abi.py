@@ -83,6 +83,10 @@ def test_host_side_validation_without_gpu(libpath):
     bad = C.make_grid((20, 12, 9), 0.05, pitch=10)  # pitch < nx
     assert C.cosmos_workspace_bytes(bad, p, C.COSMOS_OP_RK4) == 0
     assert C.lib().cosmos_rhs(ctypes.byref(bad), ctypes.byref(p), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
+    # one field's offsets must fit in 32 bits: 2^31 elements per field is refused, one row less is sized
+    huge = C.make_grid((1024, 2048, 1024), 0.05)
+    assert C.cosmos_workspace_bytes(huge, p, C.COSMOS_OP_RK4) == 0
+    assert C.cosmos_workspace_bytes(C.make_grid((1024, 2047, 1024), 0.05), p, C.COSMOS_OP_RK4) > 0
     pw = C.make_params(fluid=1, w=0.0)
     assert C.lib().cosmos_rhs(ctypes.byref(g), ctypes.byref(pw), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
 
