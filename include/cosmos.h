@@ -53,6 +53,7 @@ extern "C" {
 #define COSMOS_EWORKSPACE (-3)  /* workspace smaller than cosmos_workspace_bytes */
 #define COSMOS_EALIGN (-4)      /* pointer not 16-byte aligned */
 #define COSMOS_ENONFINITE (-5)  /* NaN/Inf or unphysical fluid state detected */
+#define COSMOS_EIO (-6)         /* a cache file could not be written */
 
 /* Workspace ops for cosmos_workspace_bytes */
 #define COSMOS_OP_RHS 0
@@ -304,6 +305,26 @@ int cosmos_batch_run(cosmos_batch plan, int first_step, int steps, int use_graph
  * Stage 1 writes only the stage buffers and accumulators, so the instance
  * states are unchanged.  Used by the autotuner. */
 int cosmos_batch_time_stage(cosmos_batch plan, int reps, double* ms_out, void* stream);
+
+/* The built-in candidate tunings of the autotuner: copies up to `max` of
+ * them into `out` (may be NULL) and returns how many there are.  Host only. */
+int cosmos_batch_default_candidates(cosmos_batch_tuning* out, int max);
+
+/* Autotuner: times every candidate tuning with cosmos_batch_time_stage
+ * (`reps` passes each, after one warm-up pass) and leaves the fastest set in
+ * the plan.  candidates = NULL with n_candidates = 0 takes the built-in list.
+ * cache_path (may be NULL): a text file with one line per key, the key being
+ * the device name, the matter model and every grid size in order.  A line for
+ * this plan's key sets its tuning without timing anything (*cache_hit = 1,
+ * ms_out filled with NaN); otherwise the search runs and the line is written
+ * (the file is rewritten through a temporary copy renamed over it).
+ * best_out (may be NULL): the chosen tuning; ms_out (n entries or NULL): the
+ * mean stage time of each candidate in ms.  Synchronous; the instance states
+ * are unchanged.  Errors: COSMOS_EINVAL (NULL plan, reps < 1, an invalid
+ * candidate), COSMOS_ECUDA, COSMOS_EIO (cache not written; the tuning is set). */
+int cosmos_batch_autotune(cosmos_batch plan, const cosmos_batch_tuning* candidates, int n_candidates, int reps,
+                          const char* cache_path, cosmos_batch_tuning* best_out, double* ms_out, int* cache_hit,
+                          void* stream);
 
 void cosmos_batch_free(cosmos_batch plan);
 

@@ -2,22 +2,24 @@
 
 ``BatchScan`` owns the instance states and the batch workspace (torch
 tensors) and drives the C ABI batch calls (``cosmos_batch_*``).
-``autotune`` times the candidate work-list mappings / launch shapes with
-``cosmos_batch_time_stage`` and keeps the fastest; results are cached in a
-JSON file keyed by the GPU name, the matter model and the grid sizes.
+``autotune`` calls the library's autotuner (``cosmos_batch_autotune``): it
+times the candidate work-list mappings / launch shapes and keeps the fastest,
+with an optional cache file keyed by the GPU name, the matter model and the
+grid sizes.
 """
 from __future__ import annotations
-
-import json
-import os
 
 import torch
 
 from . import cosmos as C
 
-# Candidate tunings: (mapping, block_x, block_y, blocks_per_sm)
+# The library's built-in candidate tunings: (mapping, block_x, block_y, blocks_per_sm)
 CANDIDATES = [(0, 32, 4, 3), (0, 16, 8, 3), (0, 64, 2, 3), (0, 8, 16, 3), (1, 32, 4, 3), (1, 32, 4, 2),
               (0, 32, 4, 2), (1, 32, 4, 1)]
+
+
+def as_tuple(t) -> tuple:
+    return (t.mapping, t.block_x, t.block_y, t.blocks_per_sm)
 
 
 def tuning(t) -> C.cosmos_batch_tuning:
@@ -73,29 +75,17 @@ class BatchScan:
         C.check(code)
         return ms
 
-    def autotune(self, candidates=CANDIDATES, reps=3, cache_path=None):
-        key = None
-        if cache_path:
-            key = json.dumps([torch.cuda.get_device_name(self.device), self.p.fluid, self.p.scalar,
-                              [(g.nx, g.ny, g.nz) for g in self.grids]])
-            if os.path.exists(cache_path):
-                cache = json.load(open(cache_path))
-                if key in cache:
-                    self.set_tuning(tuple(cache[key]["best"]))
-                    return cache[key]
-        times = {}
-        for c in candidates:
-            self.set_tuning(c)
-            times[c] = self.time_stage(reps)
-        best = min(times, key=times.get)
-        self.set_tuning(best)
-        result = {"best": list(best), "ms": {str(list(k)): v for k, v in times.items()}}
-        if cache_path:
-            cache = json.load(open(cache_path)) if os.path.exists(cache_path) else {}
-            cache[key] = result
-            with open(cache_path, "w") as f:
-                json.dump(cache, f, indent=1)
-        return result
+    def autotune(self, candidates=None, reps=3, cache_path=None):
+        """Runs the library's autotuner; candidates = None takes its built-in list.
+        Returns {"best": [...], "ms": {candidate: ms}, "cache_hit": bool} (no
+        timings on a cache hit)."""
+        cands = [tuning(c) for c in candidates] if candidates else []
+        code, best, ms, hit = C.cosmos_batch_autotune(self.plan, cands, reps, cache_path)
+        C.check(code)
+        self.tune = as_tuple(best)
+        names = [as_tuple(c) for c in (cands or C.cosmos_batch_default_candidates())]
+        return {"best": list(self.tune), "ms": {} if hit else {str(list(k)): v for k, v in zip(names, ms)},
+                "cache_hit": hit}
 
     def close(self):
         if self.plan:

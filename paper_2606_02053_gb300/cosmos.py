@@ -22,6 +22,7 @@ COSMOS_ECUDA = -2
 COSMOS_EWORKSPACE = -3
 COSMOS_EALIGN = -4
 COSMOS_ENONFINITE = -5
+COSMOS_EIO = -6
 COSMOS_OP_RHS, COSMOS_OP_RK4, COSMOS_OP_CONSTRAINTS, COSMOS_OP_INIT = 0, 1, 2, 3
 COSMOS_OP_VJP, COSMOS_OP_ADJOINT, COSMOS_OP_INIT_VJP, COSMOS_OP_DIAG = 4, 5, 6, 7
 
@@ -102,6 +103,10 @@ _SIGS = {
     "cosmos_batch_set_tuning": ([_P, ctypes.POINTER(cosmos_batch_tuning)], ctypes.c_int),
     "cosmos_batch_run": ([_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
     "cosmos_batch_time_stage": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_batch_default_candidates": ([ctypes.POINTER(cosmos_batch_tuning), ctypes.c_int], ctypes.c_int),
+    "cosmos_batch_autotune": ([_P, ctypes.POINTER(cosmos_batch_tuning), ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
+                               ctypes.POINTER(cosmos_batch_tuning), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_int), _P], ctypes.c_int),
     "cosmos_batch_free": ([_P], None),
     "cosmos_fmr_workspace_bytes": ([_FP, _PP], ctypes.c_size_t),
     "cosmos_fmr_init": ([_FP, _PP, _IDP, ctypes.POINTER(ctypes.c_void_p), _P, _S, _P], ctypes.c_int),
@@ -309,6 +314,29 @@ def cosmos_batch_time_stage(plan, reps, stream=None):
     ms = ctypes.c_double(0.0)
     code = lib().cosmos_batch_time_stage(plan, int(reps), ctypes.byref(ms), _stream(stream))
     return code, ms.value
+
+
+def cosmos_batch_default_candidates():
+    """The autotuner's built-in candidate tunings, as cosmos_batch_tuning structs."""
+    n = lib().cosmos_batch_default_candidates(None, 0)
+    arr = (cosmos_batch_tuning * n)()
+    lib().cosmos_batch_default_candidates(arr, n)
+    return list(arr)
+
+
+def cosmos_batch_autotune(plan, candidates, reps, cache_path=None, stream=None):
+    """Returns (code, best tuning, per-candidate ms, cache hit); candidates =
+    None or [] takes the library's built-in list."""
+    cands = list(candidates or [])
+    arr = (cosmos_batch_tuning * len(cands))(*cands) if cands else None
+    nms = len(cands) or lib().cosmos_batch_default_candidates(None, 0)
+    ms = (ctypes.c_double * nms)()
+    best = cosmos_batch_tuning()
+    hit = ctypes.c_int(0)
+    code = lib().cosmos_batch_autotune(plan, arr, len(cands), int(reps),
+                                       None if cache_path is None else os.fsencode(cache_path), ctypes.byref(best),
+                                       ms, ctypes.byref(hit), _stream(stream))
+    return code, best, list(ms), bool(hit.value)
 
 
 def cosmos_batch_free(plan) -> None:

@@ -1,9 +1,15 @@
 // Batched evolution of many independent grids (threshold scan): plan, run
-// (optionally as one captured CUDA graph) and the stage timing used by the
-// autotuner.  Declared in include/cosmos.h.
+// (optionally as one captured CUDA graph), the stage timing and the
+// autotuner that picks the work-list mapping and launch shape.  Declared in
+// include/cosmos.h.
+#include <math.h>
+#include <stdio.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
+#include <fstream>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -362,6 +368,134 @@ int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stre
   cudaEventDestroy(e1);
   *ms_out = ms / reps;
   return rc;
+}
+
+static const cosmos_batch_tuning kDefaultCandidates[] = {
+    {BATCH_MAP_TILE2D, 32, 4, 3}, {BATCH_MAP_TILE2D, 16, 8, 3}, {BATCH_MAP_TILE2D, 64, 2, 3},
+    {BATCH_MAP_TILE2D, 8, 16, 3}, {BATCH_MAP_LINEAR, 32, 4, 3}, {BATCH_MAP_LINEAR, 32, 4, 2},
+    {BATCH_MAP_TILE2D, 32, 4, 2}, {BATCH_MAP_LINEAR, 32, 4, 1}};
+static const int kNumDefault = (int)(sizeof(kDefaultCandidates) / sizeof(kDefaultCandidates[0]));
+
+int cosmos_batch_default_candidates(cosmos_batch_tuning* out, int max) {
+  if (out)
+    for (int i = 0; i < std::min(max, kNumDefault); ++i) out[i] = kDefaultCandidates[i];
+  return kNumDefault;
+}
+
+}  // extern "C"
+
+// Cache key of a plan: device name, matter model and every grid size, in order.
+static int cache_key(cosmos_batch b, std::string* key) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return COSMOS_ECUDA;
+  std::string k = prop.name;
+  for (char& c : k)
+    if (c == '\t' || c == '\n') c = ' ';
+  char buf[64];
+  snprintf(buf, sizeof(buf), "|fluid=%d|scalar=%d|", b->p.fluid, b->p.scalar);
+  k += buf;
+  for (int i = 0; i < b->n; ++i) {
+    snprintf(buf, sizeof(buf), "%s%dx%dx%d", i ? "," : "", b->grids[i].nx, b->grids[i].ny, b->grids[i].nz);
+    k += buf;
+  }
+  *key = k;
+  return COSMOS_OK;
+}
+
+// Cache file: one line per key, "<key>\t<mapping> <block_x> <block_y> <blocks_per_sm>\t<ms>".
+static bool cache_lookup(const char* path, const std::string& key, cosmos_batch_tuning* t) {
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t tab = line.find('\t');
+    if (tab == std::string::npos || line.compare(0, tab, key) != 0 || tab != key.size()) continue;
+    cosmos_batch_tuning c;
+    if (sscanf(line.c_str() + tab + 1, "%d %d %d %d", &c.mapping, &c.block_x, &c.block_y, &c.blocks_per_sm) == 4 &&
+        tuning_ok(&c)) {
+      *t = c;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Rewrites the file with this key's line replaced or appended (through a
+// temporary file renamed over the old one).
+static int cache_store(const char* path, const std::string& key, const cosmos_batch_tuning& t, double ms) {
+  std::vector<std::string> lines;
+  {
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line))
+      if (!(line.size() > key.size() && line.compare(0, key.size(), key) == 0 && line[key.size()] == '\t'))
+        lines.push_back(line);
+  }
+  char buf[96];
+  snprintf(buf, sizeof(buf), "\t%d %d %d %d\t%.6g", t.mapping, t.block_x, t.block_y, t.blocks_per_sm, ms);
+  lines.push_back(key + buf);
+  const std::string tmp = std::string(path) + ".tmp" + std::to_string((long)getpid());
+  {
+    std::ofstream f(tmp, std::ios::trunc);
+    for (const std::string& l : lines) f << l << '\n';
+    f.flush();
+    if (!f) {
+      remove(tmp.c_str());
+      return COSMOS_EIO;
+    }
+  }
+  if (rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return COSMOS_EIO;
+  }
+  return COSMOS_OK;
+}
+
+extern "C" {
+
+int cosmos_batch_autotune(cosmos_batch b, const cosmos_batch_tuning* candidates, int n_candidates, int reps,
+                          const char* cache_path, cosmos_batch_tuning* best_out, double* ms_out, int* cache_hit,
+                          void* stream) {
+  if (!b || reps < 1 || n_candidates < 0 || (n_candidates > 0 && !candidates)) return COSMOS_EINVAL;
+  if (n_candidates == 0) {
+    candidates = kDefaultCandidates;
+    n_candidates = kNumDefault;
+  }
+  for (int i = 0; i < n_candidates; ++i)
+    if (!tuning_ok(&candidates[i])) return COSMOS_EINVAL;
+  if (cache_hit) *cache_hit = 0;
+  std::string key;
+  if (cache_path) {
+    const int e = cache_key(b, &key);
+    if (e != COSMOS_OK) return e;
+    cosmos_batch_tuning t;
+    if (cache_lookup(cache_path, key, &t)) {
+      const int r = cosmos_batch_set_tuning(b, &t);
+      if (r != COSMOS_OK) return r;
+      if (best_out) *best_out = t;
+      if (ms_out)
+        for (int i = 0; i < n_candidates; ++i) ms_out[i] = NAN;
+      if (cache_hit) *cache_hit = 1;
+      return COSMOS_OK;
+    }
+  }
+  int best = -1;
+  double best_ms = 0.0;
+  for (int i = 0; i < n_candidates; ++i) {
+    double ms = 0.0;
+    int r = cosmos_batch_set_tuning(b, &candidates[i]);
+    if (r == COSMOS_OK) r = cosmos_batch_time_stage(b, reps, &ms, stream);
+    if (r != COSMOS_OK) return r;
+    if (ms_out) ms_out[i] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = i;
+      best_ms = ms;
+    }
+  }
+  const int r = cosmos_batch_set_tuning(b, &candidates[best]);
+  if (r != COSMOS_OK) return r;
+  if (best_out) *best_out = candidates[best];
+  return cache_path ? cache_store(cache_path, key, candidates[best], best_ms) : COSMOS_OK;
 }
 
 void cosmos_batch_free(cosmos_batch b) {

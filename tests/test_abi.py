@@ -91,6 +91,16 @@ def test_host_side_validation_without_gpu(libpath):
     assert C.lib().cosmos_rhs(ctypes.byref(g), ctypes.byref(pw), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
 
 
+def test_autotuner_candidates_without_gpu(libpath):
+    """The library's built-in candidate list (host only) is the one the Python side names."""
+    from paper_2606_02053_gb300 import batch
+    from paper_2606_02053_gb300 import cosmos as C
+
+    assert [batch.as_tuple(t) for t in C.cosmos_batch_default_candidates()] == batch.CANDIDATES
+    assert C.lib().cosmos_batch_autotune(None, None, 0, 1, None, None, None, None, None) == C.COSMOS_EINVAL
+    assert C.lib().cosmos_strerror(C.COSMOS_EIO) == b"cache file could not be written"
+
+
 def test_fmr_struct_layout_matches_c(tmp_path):
     from paper_2606_02053_gb300 import cosmos
 

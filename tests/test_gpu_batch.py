@@ -101,20 +101,31 @@ def test_batch_instance_matches_oracle(C, O):
 
 
 def test_autotune_picks_a_candidate_and_caches(C, tmp_path):
-    from paper_2606_02053_gb300.batch import CANDIDATES, BatchScan
+    from paper_2606_02053_gb300.batch import CANDIDATES, BatchScan, tuning
 
     grids, dts, ids, p = scan_setup(C, [16, 20, 18], [0.4, 0.5, 0.6])
     b = BatchScan(grids, p, dts, max_steps=1)
     b.init(ids)
     before = [s.clone() for s in b.states]
-    cache = str(tmp_path / "tune.json")
-    r = b.autotune(reps=2, cache_path=cache)
-    assert tuple(r["best"]) in CANDIDATES
-    assert all(v > 0 for v in r["ms"].values())
+    cache = tmp_path / "tune.txt"
+    cache.write_text("some other device|fluid=0|scalar=0|8x8x8\t0 32 4 3\t1.5\n")
+    r = b.autotune(reps=2, cache_path=str(cache))
+    assert tuple(r["best"]) in CANDIDATES and not r["cache_hit"]
+    assert len(r["ms"]) == len(CANDIDATES) and all(v > 0 for v in r["ms"].values())
+    assert min(r["ms"], key=r["ms"].get) == str(r["best"])
     for x, y in zip(before, b.states):  # timing passes leave the states untouched
         assert torch.equal(x, y)
-    r2 = b.autotune(reps=2, cache_path=cache)
-    assert r2["best"] == r["best"]
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 2 and lines[0].startswith("some other device")  # other keys are kept
+    assert lines[1].split("\t")[0].endswith("|fluid=1|scalar=0|16x16x16,20x20x20,18x18x18")
+    r2 = b.autotune(reps=2, cache_path=str(cache))
+    assert r2["cache_hit"] and r2["best"] == r["best"] and r2["ms"] == {}
+    assert len(cache.read_text().splitlines()) == 2
+    # an explicit candidate list; an invalid candidate is refused before anything is timed
+    r3 = b.autotune(candidates=[(1, 32, 4, 2), (0, 16, 8, 3)], reps=1)
+    assert tuple(r3["best"]) in [(1, 32, 4, 2), (0, 16, 8, 3)] and len(r3["ms"]) == 2
+    code, *_ = C.cosmos_batch_autotune(b.plan, [tuning(t) for t in [(0, 32, 4, 3), (0, 32, 8, 3)]], 1)
+    assert code == C.COSMOS_EINVAL
 
 
 def test_batch_rejects_bad_arguments(C):
