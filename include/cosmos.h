@@ -65,6 +65,7 @@ extern "C" {
 #define COSMOS_OP_ADJOINT 5
 #define COSMOS_OP_INIT_VJP 6
 #define COSMOS_OP_DIAG 7
+#define COSMOS_OP_SCAN 8
 
 typedef struct {
   int nx, ny, nz; /* grid points per direction, each >= 1 */
@@ -423,6 +424,17 @@ int cosmos_constraints_noalloc(const cosmos_grid* g, const cosmos_params* p, con
  * flop/s (2 flop per DFMA), from a timed launch of independent DFMA chains
  * on every SM.  Synchronous; allocates nothing (writes one double per thread
  * into `scratch`, which must hold 152 * 8 * 256 doubles). */
+/* Failure detection: counts, per field, the values of `state` that are NaN
+ * or Inf and, with the fluid on, the points where tau~ <= 0 (no fluid state
+ * has a non-positive energy density, so the primitive recovery has no
+ * solution there).  A reduction over the grid, never a trap; padding
+ * columns are not read.  counts_host: cosmos_nfields(p) ints, or NULL.
+ * Synchronous.  Returns COSMOS_OK when nothing was found,
+ * COSMOS_ENONFINITE when something was, else EINVAL / EALIGN / EWORKSPACE /
+ * ECUDA.  ws: COSMOS_OP_SCAN bytes. */
+int cosmos_scan_state(const cosmos_grid* g, const cosmos_params* p, const double* state, int* counts_host, void* ws,
+                      size_t ws_bytes, void* stream);
+
 int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream);
 
 /* cudaError_t of the last COSMOS_ECUDA returned by this thread. */

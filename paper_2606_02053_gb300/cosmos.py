@@ -25,6 +25,7 @@ COSMOS_ENONFINITE = -5
 COSMOS_EIO = -6
 COSMOS_OP_RHS, COSMOS_OP_RK4, COSMOS_OP_CONSTRAINTS, COSMOS_OP_INIT = 0, 1, 2, 3
 COSMOS_OP_VJP, COSMOS_OP_ADJOINT, COSMOS_OP_INIT_VJP, COSMOS_OP_DIAG = 4, 5, 6, 7
+COSMOS_OP_SCAN = 8
 
 
 class cosmos_grid(ctypes.Structure):
@@ -85,6 +86,7 @@ _SIGS = {
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_scan_state": ([_G, _PP, _P, ctypes.POINTER(ctypes.c_int), _P, _S, _P], ctypes.c_int),
     "cosmos_probe_fp64": ([_P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_adjoint_workspace_bytes": ([_G, _PP, ctypes.c_int], ctypes.c_size_t),
     "cosmos_rhs_vjp": ([_G, _PP, _P, _P, _P, _D, _P, _S, _P], ctypes.c_int),
@@ -225,6 +227,15 @@ def cosmos_constraints_noalloc(g, p, state, ham_mom, norms_out, stream=None) -> 
     """cosmos_constraints with the library's static scratch (no workspace argument)."""
     return lib().cosmos_constraints_noalloc(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(ham_mom), norms_out,
                                             _stream(stream))
+
+
+def cosmos_scan_state(g, p, state, ws=None, stream=None):
+    """Returns (code, per-field counts of non-finite values / tau~ <= 0)."""
+    nf = cosmos_nfields(p)
+    counts = (ctypes.c_int * nf)()
+    w, nb = _ws(ws)
+    code = lib().cosmos_scan_state(ctypes.byref(g), ctypes.byref(p), _ptr(state), counts, w, nb, _stream(stream))
+    return code, list(counts)
 
 
 def cosmos_probe_fp64(scratch, stream=None) -> float:

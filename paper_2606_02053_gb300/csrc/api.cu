@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "host.cuh"
 
@@ -130,6 +132,8 @@ WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
     if (op == COSMOS_OP_INIT) L.hm = take(4 * fs);
     L.partial = take(8 * n_blocks(d));
     L.final_ = take(8);
+  } else if (op == COSMOS_OP_SCAN) {
+    L.scan = take((size_t)(nf + 1) / 2);  // one 32-bit count per field
   }
   L.total_bytes = off;
   return L;
@@ -138,6 +142,29 @@ WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
 // ---------------------------------------------------------------------------
 // small kernels
 // ---------------------------------------------------------------------------
+// Per-field count of non-finite values (and, fluid on, of tau~ <= 0):
+// blockIdx.y = field; a warp-uniform grid-stride loop over the points.
+__global__ void scan_state_kernel(const DevGrid g, const double* __restrict__ U, int tau_field,
+                                  unsigned* __restrict__ counts) {
+  const int f = blockIdx.y;
+  const long npts = (long)g.nx * g.ny * g.nz;
+  const double* Uf = U + (long)f * g.fstride;
+  unsigned c = 0;
+  for (long base = (long)blockIdx.x * blockDim.x; base < npts; base += (long)gridDim.x * blockDim.x) {
+    const long q = base + threadIdx.x;
+    bool bad = false;
+    if (q < npts) {
+      const int i = (int)(q % g.nx);
+      const long r = q / g.nx;
+      const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+      const double v = Uf[((long)k * g.ny + j) * g.pitch + i];
+      bad = !isfinite(v) || (f == tau_field && !(v > 0.0));
+    }
+    c += __popc(__ballot_sync(0xffffffffu, bad));
+  }
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(counts + f, c);
+}
+
 __global__ void reduce_partials(const double* __restrict__ part, long nb, double* __restrict__ out) {
   // one block of 256 threads; fixed summation order
   __shared__ double s[256][8];
@@ -642,6 +669,37 @@ int cosmos_constraints(const cosmos_grid* g, const cosmos_params* p, const doubl
     norms_host[4 + m] = r[4 + m];
   }
   return COSMOS_OK;
+}
+
+int cosmos_scan_state(const cosmos_grid* g, const cosmos_params* p, const double* state, int* counts_host, void* ws,
+                      size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state) return COSMOS_EINVAL;
+  if (!aligned16(state)) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_SCAN);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nf = 24 + 4 * p->fluid + 2 * p->scalar;
+  unsigned* counts = (unsigned*)((double*)ws + L.scan);
+  CK(cudaMemsetAsync(counts, 0, nf * sizeof(unsigned), s));
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const DevGrid d = make_devgrid(g);
+  const long npts = (long)g->nx * g->ny * g->nz;
+  const long per_field = std::max(1L, std::min((long)(4 * sms / nf + 1), (npts + 255) / 256));
+  scan_state_kernel<<<dim3((unsigned)per_field, nf), 256, 0, s>>>(d, state, p->fluid ? 24 : -1, counts);
+  CK(cudaGetLastError());
+  unsigned h[30];
+  CK(cudaMemcpyAsync(h, counts, nf * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  bool any = false;
+  for (int f = 0; f < nf; ++f) {
+    if (counts_host) counts_host[f] = (int)h[f];
+    any = any || h[f];
+  }
+  return any ? COSMOS_ENONFINITE : COSMOS_OK;
 }
 
 int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream) {

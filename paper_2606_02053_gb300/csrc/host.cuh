@@ -9,7 +9,7 @@ namespace cosmos {
 // Workspace sub-buffers of the single-grid calls (each 256-byte aligned), in
 // doubles from the workspace pointer; total_bytes is the size the op needs.
 struct WsLayout {
-  size_t prim, flux, D, stageA, stageB, acc, hm, partial, final_, limbs, expo, total_bytes;
+  size_t prim, flux, D, stageA, stageB, acc, hm, partial, final_, limbs, expo, scan, total_bytes;
 };
 WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op);
 int check_ws(const WsLayout& L, void* ws, size_t ws_bytes);  // COSMOS_OK, EINVAL, EWORKSPACE or EALIGN

@@ -61,6 +61,15 @@ class Evolution:
         for n in range(steps):
             C.check(C.cosmos_rk4_step(self.g, self.p, self.state, t + n * dt, dt, self.ws_rk4))
 
+    def scan(self):
+        """Failure detection on the current state: {field: count} of NaN/Inf
+        values (and, fluid on, of tau~ <= 0); empty when the state is sound."""
+        ws = _alloc_ws(C.cosmos_workspace_bytes(self.g, self.p, C.COSMOS_OP_SCAN), self.device)
+        code, counts = C.cosmos_scan_state(self.g, self.p, self.state, ws)
+        if code not in (C.COSMOS_OK, C.COSMOS_ENONFINITE):
+            C.check(code)
+        return {f: c for f, c in enumerate(counts) if c}
+
     def constraints(self, want_fields=False):
         hm = torch.empty(4 * self.fs, dtype=torch.float64, device=self.device) if want_fields else None
         norms = (ctypes.c_double * 8)()

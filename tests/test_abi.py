@@ -91,6 +91,21 @@ def test_host_side_validation_without_gpu(libpath):
     assert C.lib().cosmos_rhs(ctypes.byref(g), ctypes.byref(pw), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
 
 
+def test_state_scan_host_checks_without_gpu(libpath):
+    """The failure-detection scan sizes its workspace (one count per field) and
+    refuses bad arguments before touching the device."""
+    from paper_2606_02053_gb300 import cosmos as C
+
+    g = C.make_grid((20, 12, 9), 0.05, pitch=24)
+    for p, nf in ((C.make_params(), 24), (C.make_params(fluid=1, scalar=1), 30)):
+        assert C.cosmos_workspace_bytes(g, p, C.COSMOS_OP_SCAN) == 256 * ((4 * nf + 255) // 256)
+    p = C.make_params(fluid=1)
+    counts = (ctypes.c_int * 28)()
+    assert C.lib().cosmos_scan_state(ctypes.byref(g), ctypes.byref(p), None, counts, None, 0, None) == C.COSMOS_EINVAL
+    assert C.lib().cosmos_scan_state(ctypes.byref(g), ctypes.byref(p), 8, counts, None, 0, None) == C.COSMOS_EALIGN
+    assert C.lib().cosmos_scan_state(ctypes.byref(g), ctypes.byref(p), 256, counts, None, 0, None) == C.COSMOS_EINVAL
+
+
 def test_autotuner_candidates_without_gpu(libpath):
     """The library's built-in candidate list (host only) is the one the Python side names."""
     from paper_2606_02053_gb300 import batch
