@@ -39,14 +39,15 @@ BYTES_PER_POINT_STAGE = [8 * 3 * 24, 8 * 5 * 24, 8 * 5 * 24, 8 * 4 * 24]
 COMBINE_FLOPS = [2, 4, 4, 3]
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # each pass of the vacuum stage, from the committed ncu capture of the 96^3
-# case (the derivative pass: exponent scan + limb conversion + integer pass),
-# and the hash of the kernel sources it was taken on.  Reported scaled to the
-# bench grid by points; null when the kernel sources differ from the profiled
-# ones.
-NCU_TRAFFIC = {"sources_sha256_16": "edae325199ba735e", "grid": 96,
-               "bytes_per_launch": {"derivative": (169890048 + 54016) + (169882880 + 122339072)
-                                    + (241765120 + 1106756000),
-                                    "algebra": 1377657000 + 800894208}}
+# case (the derivative pass: exponent scan + limb conversion + integer pass;
+# the algebra pass: the mean over a step's stages 1, 2, 3, 4), and the hash of
+# the kernel sources it was taken on.  Reported scaled to the bench grid by
+# points; null when the kernel sources differ from the profiled ones.
+NCU_TRAFFIC = {"sources_sha256_16": "b5d37d4ebf1c1ba7", "grid": 96,
+               "bytes_per_launch": {"derivative": (169887488 + 46080) + (169918976 + 122176256)
+                                    + (239166976 + 1097534208),
+                                    "algebra": ((1377657000 + 800894208) + 2 * (1685224192 + 698256896)
+                                                + (1673015296 + 477257216)) / 4}}
 # derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
 DERIV_DOUBLES = 162
 KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_int.cuh", "limbs.cu", "stage_vac.cu",

@@ -287,6 +287,13 @@ int cosmos_batch_set_tuning(cosmos_batch b, const cosmos_batch_tuning* tuning) {
 // persistent grid of the integer derivative pass: its resident blocks on every SM
 static int ideriv_blocks(cosmos_batch b) { return b->sms * COSMOS_IDERIV_MIN_BLOCKS; }
 
+// every grid of the batch admits the integer pass's division-free periodic wrap
+static bool ideriv_near(cosmos_batch b) {
+  for (int i = 0; i < b->n; ++i)
+    if (!near_indices(make_devgrid(&b->grids[i]))) return false;
+  return true;
+}
+
 static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStream_t s) {
   BatchStageLauncher launch = launch_batch_stage_vac;
   if (b->p.fluid && b->p.scalar)
@@ -306,7 +313,7 @@ static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStr
       const double* kref = b->d_kref + ((size_t)st * 4 + stage) * b->n;
       if (launch_batch_limbs(args, b->n, nslot_of(&b->p), b->p.fluid, (int*)(b->ws + b->L.expo), s) != cudaSuccess ||
           launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s, b->d_dtiles,
-                 b->ndtiles, ideriv_blocks(b)) != cudaSuccess)
+                 b->ndtiles, ideriv_blocks(b), ideriv_near(b)) != cudaSuccess)
         return COSMOS_ECUDA;
     }
   return COSMOS_OK;
@@ -357,7 +364,7 @@ int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stre
     if (rc == COSMOS_OK &&
         (launch_batch_limbs(b->d_args, b->n, nslot_of(&b->p), b->p.fluid, (int*)(b->ws + b->L.expo), s) != cudaSuccess ||
          launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s, b->d_dtiles,
-                b->ndtiles, ideriv_blocks(b)) != cudaSuccess))
+                b->ndtiles, ideriv_blocks(b), ideriv_near(b)) != cudaSuccess))
       rc = COSMOS_ECUDA;
   }
   cudaEventRecord(e1, s);

@@ -134,16 +134,18 @@ cudaError_t launch_stage_scalar(const StageArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_stage_fluid_scalar(const StageArgs& a, int mode, cudaStream_t s);
 // batched stage: derivative pass over the BX x DBY tile list (dtiles), algebra
 // pass over the tuned work list (tiles, mapping)
+// (last two: resident blocks of the integer derivative pass, 0 for the FP64
+// pass; whether near_indices holds for every grid of the batch)
 typedef cudaError_t (*BatchStageLauncher)(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
-                                          dim3, cudaStream_t, const BatchTile*, long, int);
+                                          dim3, cudaStream_t, const BatchTile*, long, int, bool);
 cudaError_t launch_batch_stage_vac(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                   cudaStream_t, const BatchTile*, long, int);
+                                   cudaStream_t, const BatchTile*, long, int, bool);
 cudaError_t launch_batch_stage_fluid(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                     cudaStream_t, const BatchTile*, long, int);
+                                     cudaStream_t, const BatchTile*, long, int, bool);
 cudaError_t launch_batch_stage_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3, dim3,
-                                      cudaStream_t, const BatchTile*, long, int);
+                                      cudaStream_t, const BatchTile*, long, int, bool);
 cudaError_t launch_batch_stage_fluid_scalar(const StageArgs*, const BatchTile*, long, int, const double*, int, dim3,
-                                            dim3, cudaStream_t, const BatchTile*, long, int);
+                                            dim3, cudaStream_t, const BatchTile*, long, int, bool);
 cudaError_t launch_batch_fluid(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping, double w,
                                dim3 grid, dim3 block, cudaStream_t s);
 cudaError_t launch_constraints_vac(const ConstraintArgs& a, cudaStream_t s);
@@ -177,5 +179,12 @@ inline dim3 point_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.
 inline dim3 deriv_grid(const DevGrid& g) {
   return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, (g.nz + DBZ - 1) / DBZ);
 }
+// integer derivative pass: one BX x DBY tile of one z-plane per block
+inline dim3 ideriv_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, g.nz); }
+// Every index the integer derivative pass forms for a tile lies in [-n, 2n)
+// along each axis, so one compare and select wraps it (stage_int.cuh,
+// wrap_near): x in [i0 - 3, i0 + BX + 2] with i0 <= nx - 1, y in
+// [j0 - 3, j0 + DBY + 2] with j0 <= ny - 1, z in [k - 3, k + 3] with k <= nz - 1.
+__host__ __device__ inline bool near_indices(const DevGrid& g) { return g.nx >= BX + 3 && g.ny >= DBY + 3 && g.nz >= 3; }
 
 }  // namespace cosmos

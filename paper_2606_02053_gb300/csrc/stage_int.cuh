@@ -126,18 +126,27 @@ struct NbrI {
   int c;
 };
 
+// Periodic index of a in [-n, 2n): a compare and a select instead of the
+// integer division of wrap_index.
+__device__ __forceinline__ int wrap_near(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <bool NEAR>
+__device__ __forceinline__ int wrap_i(int a, int n) { return NEAR ? wrap_near(a, n) : wrap_index(a, n); }
+
+template <bool NEAR>
 __device__ __forceinline__ NbrI make_nbri(const DevGrid& g, int i, int j, int k) {
   NbrI n;
   const int row = g.pitch, plane = g.pitch * g.ny;
 #pragma unroll
   for (int o = -3; o <= 3; ++o) {
-    n.x[o + 3] = wrap_index(i + o, g.nx);
-    n.y[o + 3] = wrap_index(j + o, g.ny) * row;
-    n.z[o + 3] = wrap_index(k + o, g.nz) * plane;
+    n.x[o + 3] = wrap_i<NEAR>(i + o, g.nx);
+    n.y[o + 3] = wrap_i<NEAR>(j + o, g.ny) * row;
+    n.z[o + 3] = wrap_i<NEAR>(k + o, g.nz) * plane;
   }
   n.c = n.z[3] + n.y[3] + n.x[3];
   return n;
 }
+
 
 template <int D>
 __device__ __forceinline__ int dispi(const NbrI& n, int o) {
@@ -146,28 +155,33 @@ __device__ __forceinline__ int dispi(const NbrI& n, int o) {
   return n.z[o + 3] + n.y[3] + n.x[3];
 }
 
+template <bool NEAR>
 __device__ __forceinline__ int limb_plane_off(const DevGrid& g, int x, int y, int k) {
-  return (wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
+  return (wrap_i<NEAR>(k, g.nz) * g.ny + wrap_i<NEAR>(y, g.ny)) * g.pitch + wrap_i<NEAR>(x, g.nx);
 }
 
 // Digit sums of D_y (rows j0 .. j0+DBY-1) and D_z (rows j0-2 .. j0+DBY+1) on
 // the x-extended tile (halo 2), unscaled.
-__device__ __forceinline__ void stage_dydz_int(const DevGrid& g, const long long* __restrict__ Lf, int i0, int j0, int k,
-                                               int tid, int3* __restrict__ sDy, int3* __restrict__ sDz) {
+template <bool NEAR>
+__device__ __forceinline__ void stage_dydz_int(const DevGrid& g, const long long* __restrict__ Lf, int i0, int j0,
+                                                 int k, int tid, int3* __restrict__ sDy, int3* __restrict__ sDz) {
   constexpr int TXH = BX + 4;
   for (int q = tid; q < TXH * DBY; q += BX * DBY) {
     const int qx = q % TXH, qy = q / TXH;
     const int x = i0 - 2 + qx, y = j0 + qy;
-    sDy[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off(g, x, y + 1, k)), ldl(Lf, limb_plane_off(g, x, y - 1, k))), 8),
-                   l_sub(ldl(Lf, limb_plane_off(g, x, y + 2, k)), ldl(Lf, limb_plane_off(g, x, y - 2, k))));
+    sDy[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y + 1, k)),
+                               ldl(Lf, limb_plane_off<NEAR>(g, x, y - 1, k))), 8),
+                   l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y + 2, k)), ldl(Lf, limb_plane_off<NEAR>(g, x, y - 2, k))));
   }
   for (int q = tid; q < TXH * (DBY + 4); q += BX * DBY) {
     const int qx = q % TXH, qy = q / TXH;
     const int x = i0 - 2 + qx, y = j0 - 2 + qy;
-    sDz[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off(g, x, y, k + 1)), ldl(Lf, limb_plane_off(g, x, y, k - 1))), 8),
-                   l_sub(ldl(Lf, limb_plane_off(g, x, y, k + 2)), ldl(Lf, limb_plane_off(g, x, y, k - 2))));
+    sDz[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y, k + 1)),
+                               ldl(Lf, limb_plane_off<NEAR>(g, x, y, k - 1))), 8),
+                   l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y, k + 2)), ldl(Lf, limb_plane_off<NEAR>(g, x, y, k - 2))));
   }
 }
+
 
 // Neighbour sums of one axis at point n: D1 sum 8 (f+1 - f-1) - (f+2 - f-2)
 // and s_k = f(+k) + f(-k), k = 1, 2, 3 (each neighbour loaded once).
@@ -270,13 +284,13 @@ __device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, cons
 
 // One BX x DBY tile of one z-plane (block of BX x DBY threads), as deriv_tile
 // with the staging of one second-derivative field at a time.
-template <class T>
+template <class T, bool NEAR>
 __device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, int k, int3* __restrict__ sDy,
                                             int3* __restrict__ sDz) {
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int i = i0 + tx, j = j0 + ty;
   const bool valid = i < a.g.nx && j < a.g.ny;
-  const NbrI n = make_nbri(a.g, i, j, k);
+  const NbrI n = make_nbri<NEAR>(a.g, i, j, k);
   const long fs = a.g.fstride;
   const bool ko_equal = a.c.ko[0] == a.c.ko[1] && a.c.ko[1] == a.c.ko[2];
   const int f_lo = a.f_lo, f_hi = a.f_hi > 0 ? a.f_hi : (1 << 30);
@@ -290,27 +304,28 @@ __device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, 
   for (int m2 = 0; m2 < T::ND2; ++m2) {
     const int f = T::d2_field(m2);
     if (f < f_lo || f >= f_hi) continue;  // uniform across the block
-    stage_dydz_int(a.g, a.L + (long)ko_slot<T>(f) * fs, i0, j0, k, tid, sDy, sDz);
+    stage_dydz_int<NEAR>(a.g, a.L + (long)ko_slot<T>(f) * fs, i0, j0, k, tid, sDy, sDz);
     __syncthreads();
     if (valid) ideriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy, sDz);
     __syncthreads();
   }
 }
 
-template <class T>
+// NEAR: near_indices holds for the grid (for every grid of a batch).
+template <class T, bool NEAR>
 __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS) ideriv_kernel(const StageArgs a) {
   __shared__ int3 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
-  ideriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
+  ideriv_tile<T, NEAR>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
 }
 
 // Persistent batched integer derivative pass over BX x DBY tiles of every instance.
-template <class T>
+template <class T, bool NEAR>
 __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS)
     batch_ideriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
   __shared__ int3 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
   for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
     const BatchTile t = tiles[w];
-    ideriv_tile<T>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);
+    ideriv_tile<T, NEAR>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);
   }
 }
 

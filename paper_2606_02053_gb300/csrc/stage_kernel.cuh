@@ -550,8 +550,10 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
     dim3 grid = point_grid(a.g), block(BX, BY);                                                                \
     if (a.k_cnt > 0) grid.z = a.k_cnt;                                                                          \
     if (mode < 0 || !(mode & 8)) {                                                                            \
-      if (a.L)                                                                                                  \
-        ideriv_kernel<T_##NAME><<<dim3(deriv_grid(a.g).x, deriv_grid(a.g).y, a.g.nz), dim3(BX, DBY), 0, s>>>(a); \
+      if (a.L && near_indices(a.g))                                                                            \
+        ideriv_kernel<T_##NAME, true><<<ideriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);                            \
+      else if (a.L)                                                                                             \
+        ideriv_kernel<T_##NAME, false><<<ideriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);                           \
       else                                                                                                      \
         deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY, DBZ), 0, s>>>(a);                               \
     }                                                                                                           \
@@ -566,9 +568,12 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
   }                                                                                                             \
   cudaError_t launch_batch_stage_##NAME(const StageArgs* args, const BatchTile* tiles, long ntiles, int mapping,  \
                                         const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s,      \
-                                        const BatchTile* dtiles, long ndtiles, int ideriv_blocks) {               \
-    if (ideriv_blocks > 0)                                                                                      \
-      batch_ideriv_kernel<T_##NAME><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);             \
+                                        const BatchTile* dtiles, long ndtiles, int ideriv_blocks,                 \
+                                        bool ideriv_near) {                                                       \
+    if (ideriv_blocks > 0 && ideriv_near)                                                                       \
+      batch_ideriv_kernel<T_##NAME, true><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);       \
+    else if (ideriv_blocks > 0)                                                                                 \
+      batch_ideriv_kernel<T_##NAME, false><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);      \
     else                                                                                                        \
       batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY, DBZ), 0, s>>>(args, dtiles, ndtiles);                  \
     switch (mode) {                                                                                             \

@@ -109,3 +109,17 @@ def test_non_finite_value_is_not_hidden(C, O):
     r = ev.get(ev.rhs(0.0))
     # the field's derivatives (its advection and KO terms) are NaN at every point, not finite numbers
     assert np.isnan(r[8]).all()
+
+
+@pytest.mark.parametrize("n", [(35, 11, 3), (34, 11, 3), (35, 10, 3), (35, 11, 2), (70, 19, 5)])
+def test_periodic_wrap_on_both_sides_of_the_division_free_threshold(C, O, n):
+    """The pass wraps its periodic neighbour indices with one compare and
+    select when every index of a tile lies in [-n, 2n) (nx >= 35, ny >= 11,
+    nz >= 3), else by integer division; grids on both sides of that line,
+    with tiles that overhang the grid's end, against the oracle."""
+    from paper_2606_02053_gb300 import inputs
+
+    s = inputs.smooth_state(n, seed=905 + sum(n))
+    p = C.make_params(slicing=0, shift=1, eta=1.1, ko_sigma=0.15)
+    r, ref = rhs_both(C, O, s, p, n)
+    assert field_errors(r, ref).max() <= RHS_TOL
