@@ -53,7 +53,8 @@ extern "C" {
 #define COSMOS_EWORKSPACE (-3)  /* workspace smaller than cosmos_workspace_bytes */
 #define COSMOS_EALIGN (-4)      /* pointer not 16-byte aligned */
 #define COSMOS_ENONFINITE (-5)  /* NaN/Inf or unphysical fluid state detected */
-#define COSMOS_EIO (-6)         /* a cache file could not be written */
+#define COSMOS_EIO (-6)         /* a file could not be opened, read or written */
+#define COSMOS_ECHECKPOINT (-7) /* checkpoint of another grid / parameters, or corrupt */
 
 /* Workspace ops for cosmos_workspace_bytes */
 #define COSMOS_OP_RHS 0
@@ -441,6 +442,32 @@ int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream);
 int cosmos_last_cuda_error(void);
 
 /* Static description of an error code. */
+/* ------------------------------------------------------------------------
+ * Checkpoint / resume of one grid's state.  File: a 4096-byte text header
+ * (one JSON object, padded with spaces, ending in a newline: "format"
+ * "cosmos-checkpoint", "version" 1, "byte_order", "n" [nx, ny, nz], "h",
+ * "x0", "nfields", "fields" (names in state order), "params" (slicing, shift,
+ * fluid, scalar, eta, ko_sigma, w, H0, t0), "t", "step", "payload_bytes",
+ * "payload_fnv1a64" (hex)), then every field as nx * ny * nz binary64 values,
+ * i fastest, field after field (padding columns not stored).  Doubles in the
+ * header carry 17 significant digits, so they read back exactly.
+ * state_on_device: 1 for a device buffer (copied through host memory on
+ * `stream`, synchronously), 0 for a host buffer of the same pitched layout.
+ * ------------------------------------------------------------------------ */
+
+/* Writes `path` through a temporary file "<path>.partial" renamed over it.
+ * Errors: COSMOS_EINVAL, COSMOS_EIO, COSMOS_ECUDA. */
+int cosmos_checkpoint_save(const char* path, const cosmos_grid* g, const cosmos_params* p, const double* state,
+                           int state_on_device, double t, long long step, void* stream);
+
+/* Reads `path` into `state` and returns its time and step counter.  The
+ * header must give exactly this grid (sizes, spacing, origin) and these
+ * parameters, and the payload must have the stated size and hash, else
+ * COSMOS_ECHECKPOINT and `state` is not written.  Errors also COSMOS_EINVAL,
+ * COSMOS_EIO, COSMOS_ECUDA. */
+int cosmos_checkpoint_load(const char* path, const cosmos_grid* g, const cosmos_params* p, double* state,
+                           int state_on_device, double* t_out, long long* step_out, void* stream);
+
 const char* cosmos_strerror(int code);
 
 #ifdef __cplusplus

@@ -23,6 +23,7 @@ COSMOS_EWORKSPACE = -3
 COSMOS_EALIGN = -4
 COSMOS_ENONFINITE = -5
 COSMOS_EIO = -6
+COSMOS_ECHECKPOINT = -7
 COSMOS_OP_RHS, COSMOS_OP_RK4, COSMOS_OP_CONSTRAINTS, COSMOS_OP_INIT = 0, 1, 2, 3
 COSMOS_OP_VJP, COSMOS_OP_ADJOINT, COSMOS_OP_INIT_VJP, COSMOS_OP_DIAG = 4, 5, 6, 7
 COSMOS_OP_SCAN = 8
@@ -86,6 +87,10 @@ _SIGS = {
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "cosmos_checkpoint_save": ([ctypes.c_char_p, _G, _PP, _P, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, _P],
+                               ctypes.c_int),
+    "cosmos_checkpoint_load": ([ctypes.c_char_p, _G, _PP, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_longlong), _P], ctypes.c_int),
     "cosmos_scan_state": ([_G, _PP, _P, ctypes.POINTER(ctypes.c_int), _P, _S, _P], ctypes.c_int),
     "cosmos_probe_fp64": ([_P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_adjoint_workspace_bytes": ([_G, _PP, ctypes.c_int], ctypes.c_size_t),
@@ -227,6 +232,30 @@ def cosmos_constraints_noalloc(g, p, state, ham_mom, norms_out, stream=None) -> 
     """cosmos_constraints with the library's static scratch (no workspace argument)."""
     return lib().cosmos_constraints_noalloc(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(ham_mom), norms_out,
                                             _stream(stream))
+
+
+def _state_arg(state):
+    """(pointer, on_device) of a torch tensor (CUDA or CPU) or a C-contiguous numpy array."""
+    if hasattr(state, "data_ptr"):
+        return ctypes.c_void_p(state.data_ptr()), int(state.is_cuda)
+    return ctypes.c_void_p(state.ctypes.data), 0
+
+
+def cosmos_checkpoint_save(path, g, p, state, t, step, stream=None) -> int:
+    """state: a device tensor, or a host tensor / numpy array, in the state layout."""
+    ptr, dev = _state_arg(state)
+    return lib().cosmos_checkpoint_save(os.fsencode(path), ctypes.byref(g), ctypes.byref(p), ptr, dev, float(t),
+                                        int(step), _stream(stream) if dev else None)
+
+
+def cosmos_checkpoint_load(path, g, p, state, stream=None):
+    """Returns (code, t, step); state is overwritten only on success."""
+    ptr, dev = _state_arg(state)
+    t = ctypes.c_double(0.0)
+    step = ctypes.c_longlong(0)
+    code = lib().cosmos_checkpoint_load(os.fsencode(path), ctypes.byref(g), ctypes.byref(p), ptr, dev,
+                                        ctypes.byref(t), ctypes.byref(step), _stream(stream) if dev else None)
+    return code, t.value, step.value
 
 
 def cosmos_scan_state(g, p, state, ws=None, stream=None):

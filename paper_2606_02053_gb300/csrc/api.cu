@@ -736,7 +736,8 @@ const char* cosmos_strerror(int code) {
     case COSMOS_EWORKSPACE: return "workspace too small";
     case COSMOS_EALIGN: return "pointer not aligned (16 bytes; workspace 256 bytes)";
     case COSMOS_ENONFINITE: return "non-finite or unphysical state";
-    case COSMOS_EIO: return "cache file could not be written";
+    case COSMOS_EIO: return "file could not be opened, read or written";
+    case COSMOS_ECHECKPOINT: return "checkpoint of another grid or parameters, or corrupt";
     default: return "unknown error code";
   }
 }

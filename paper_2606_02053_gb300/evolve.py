@@ -61,6 +61,16 @@ class Evolution:
         for n in range(steps):
             C.check(C.cosmos_rk4_step(self.g, self.p, self.state, t + n * dt, dt, self.ws_rk4))
 
+    def save(self, path, t, step):
+        """Checkpoint of the current state (cosmos_checkpoint_save)."""
+        C.check(C.cosmos_checkpoint_save(path, self.g, self.p, self.state, t, step))
+
+    def load(self, path):
+        """Resume from a checkpoint of this grid and these parameters; returns (t, step)."""
+        code, t, step = C.cosmos_checkpoint_load(path, self.g, self.p, self.state)
+        C.check(code)
+        return t, step
+
     def scan(self):
         """Failure detection on the current state: {field: count} of NaN/Inf
         values (and, fluid on, of tau~ <= 0); empty when the state is sound."""

@@ -113,7 +113,7 @@ def test_autotuner_candidates_without_gpu(libpath):
 
     assert [batch.as_tuple(t) for t in C.cosmos_batch_default_candidates()] == batch.CANDIDATES
     assert C.lib().cosmos_batch_autotune(None, None, 0, 1, None, None, None, None, None) == C.COSMOS_EINVAL
-    assert C.lib().cosmos_strerror(C.COSMOS_EIO) == b"cache file could not be written"
+    assert C.lib().cosmos_strerror(C.COSMOS_EIO) == b"file could not be opened, read or written"
 
 
 def test_fmr_struct_layout_matches_c(tmp_path):
