@@ -422,3 +422,42 @@ def test_fluid_primitive_recovery_round_trip(O):
         # E^2 - J^2 = (rho + P)^2 W^2 - ... cancels as v -> 1: the recovery's condition
         # number grows like W^4, so the bound does too (a wrong formula is off by O(1))
         assert np.all(np.abs(got - rho) <= 4e-15 * W2 * W2 * rho), (w, np.max(np.abs(got / rho - 1)))
+
+
+# ---------------------------------------------------------------------------
+# Conservation: on a flat, static background (chi = 1, gt = delta, K = 0,
+# alpha = 1, beta = 0) the fluid's geometric sources vanish, so the fluid
+# right-hand side is minus the divergence of the Kurganov-Tadmor face fluxes
+# plus the Kreiss-Oliger term; on a periodic grid both telescope, and the grid
+# sums of the tau~ and S~_i right-hand sides vanish for any fluid state.  A flux
+# that is not the same on both sides of a face (a non-conservative form, an
+# upwinding on one side only, a wrong face index) breaks the sum.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("ko", [0.0, 0.2])
+def test_kt_fluid_totals_are_conserved_on_a_flat_background(O, ko):
+    n = (12, 10, 9)
+    P = O.params_array(slicing=0, shift=1, ko_sigma=ko, w=1.0 / 3.0, fluid=1)
+    s = flat_state(O, n, P)
+    rng = np.random.default_rng(77)
+    E = 1.0 + 0.5 * rng.random((n[2], n[1], n[0]))
+    J = 0.4 * (rng.random((3, n[2], n[1], n[0])) - 0.5) * E  # |J| <= 0.35 E: a physical state
+    s[24] = E
+    s[25:28] = J
+    r = O.rhs(O.OGrid(n, 1.0 / n[0]), P, s)
+    for f in range(24, 28):
+        total, scale = r[f].sum(), np.abs(r[f]).sum()
+        assert scale > 1.0
+        assert abs(total) <= 1e-13 * scale, (f, total, scale)
+
+
+def test_kt_conservation_pin_catches_a_one_sided_flux(O):
+    """The same sum with a planted non-conservative term (the first face of
+    every cell weighted 1 + 1e-6) is far from zero: the pin can fail."""
+    n = 12
+    rng = np.random.default_rng(78)
+    E = 1.0 + 0.5 * rng.random(n)
+    H = E + 0.1 * np.roll(E, -1)  # any face flux H_{i+1/2}
+    good = -(H - np.roll(H, 1))
+    bad = -(H - (1 + 1e-6) * np.roll(H, 1))
+    assert abs(good.sum()) <= 1e-13 * np.abs(good).sum()
+    assert abs(bad.sum()) > 1e-8 * np.abs(bad).sum()
