@@ -87,11 +87,12 @@ def face_flux(d: int):
         hW2 = (rho + P) * W2
         E = hW2 - P
         J = [hW2 * v[i] for i in range(3)]
-        Ui = [sqrtg * E] + [sqrtg * J[i] for i in range(3)]
-        Fi = [sqrtg * (alpha * hW2 * vu[d] - betad * E)]
+        # densitised by sqrt(gamma) once per face, below, instead of per component
+        Ui = [E] + [J[i] for i in range(3)]
+        Fi = [alpha * hW2 * vu[d] - betad * E]
         for i in range(3):
             Sdi = hW2 * vu[d] * v[i] + (P if i == d else 0.0)
-            Fi.append(sqrtg * (alpha * Sdi - betad * J[i]))
+            Fi.append(alpha * Sdi - betad * J[i])
         disc = (1.0 - v2) * (gu[PIDX[(d, d)]] * (1.0 - v2 * w) - vu[d] * vu[d] * one_m_w)
         root = sqw * sqrt(disc)
         pre = alpha * (1.0 - v2 * w).rcp()
@@ -101,5 +102,6 @@ def face_flux(d: int):
         F.append(Fi)
         lam.append((lp, lm))
     a = fmax(fmax(fabs(lam[0][0]), fabs(lam[0][1])), fmax(fabs(lam[1][0]), fabs(lam[1][1])))
-    out = [0.5 * (F[0][m] + F[1][m]) - 0.5 * a * (U[1][m] - U[0][m]) for m in range(4)]
+    hs = 0.5 * sqrtg
+    out = [hs * ((F[0][m] + F[1][m]) - a * (U[1][m] - U[0][m])) for m in range(4)]
     return g, names, out
