@@ -260,6 +260,25 @@ int cosmos_compaction(const cosmos_grid* g, const cosmos_params* p, const double
 int cosmos_compaction_vjp(const cosmos_grid* g, const cosmos_params* p, const double* state, int kstar, int kmax,
                           const double* aux_host, double cbar, double* lam, void* stream);
 
+/* Central lapse of a run (the collapse diagnostic the paper's PBH examples
+ * follow, section "Examples": the lapse at the centre of the overdensity
+ * falls as it collapses).  Copies alpha at the centre grid point
+ * (nx/2, ny/2, nz/2) of `state` into series[index] (device memory, at least
+ * index + 1 doubles).  Asynchronous.  Errors: COSMOS_EINVAL. */
+int cosmos_central_lapse(const cosmos_grid* g, const cosmos_params* p, const double* state, double* series,
+                         int index, void* stream);
+
+/* Reverse of cosmos_central_lapse: lam[alpha at the centre point] += abar
+ * (lam in state layout, device).  Asynchronous. */
+int cosmos_central_lapse_vjp(const cosmos_grid* g, const cosmos_params* p, double abar, double* lam, void* stream);
+
+/* Minimum of series[0 .. count-1] (device) and the first index attaining
+ * it: result[0] = the minimum, result[1] = its index as a double (device,
+ * 2 doubles).  One warp scans in a fixed order (deterministic); a NaN
+ * entry never wins against a number.  Asynchronous.  Errors: COSMOS_EINVAL
+ * (NULL pointer, count < 1). */
+int cosmos_series_argmin(const double* series, int count, double* result, void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched evolution of many independent grids (a threshold scan: one
  * instance per amplitude or shape of the initial perturbation, grids of

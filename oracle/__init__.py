@@ -20,6 +20,15 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   fluid_rho   : round trip (rho, v) -> (E, J) -> rho against the definitions.
   rhs_vjp / adjoint_step : tape reverse mode of rhs / rk4_step; pinned by
       finite-difference dot-product tests against the (pinned) forward map.
+  init_zeta / compaction / central_lapse (collapse diagnostics): the zeta map
+      equals the Gaussian initial data when given the Gaussian's values and
+      leaves H = 0, M = 0; compaction is 0 for a homogeneous state and equals
+      the closed form 2 dM / R of a top-hat overdensity (lattice counts by
+      brute force); the areal radius uses exactly the six axis points.
+  init_zeta_vjp / compaction_vjp / collapse_gradient : tapes over the same
+      functions, pinned by finite-difference dot-product tests; the whole
+      pipeline zeta -> (min central lapse, peak compaction) against central
+      differences along the amplitude mu.
   fmr_* (fixed mesh refinement) : prolongation exact for degree-5
       polynomials and not for degree 6; injection against its definition;
       the RK4 continuous extension against quadrature and linear-ODE closed
@@ -348,3 +357,120 @@ def fmr_interior(level):
     m = np.zeros((n[2], n[1], n[0]), dtype=bool)
     m[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
     return m
+
+
+# --------------------------------------------------------------------------
+# Collapse diagnostics and initial data from a per-point zeta (definitions in
+# cosmos_oracle.cpp, section "Collapse diagnostics"), with their reverse modes
+# and the whole pipeline zeta -> N RK4 steps -> (min central lapse, peak
+# compaction) reversed through the oracle's own tapes.
+# --------------------------------------------------------------------------
+def _diag_lib():
+    L = lib()
+    if not getattr(L, "_diag_sigs", False):
+        G = [_I, _D, _D, _D]
+        L.oracle_init_zeta.argtypes = G + [_D, ctypes.c_double, _D]
+        L.oracle_init_zeta_vjp.argtypes = G + [_D, ctypes.c_double, _D, _D]
+        L.oracle_central_lapse.argtypes = [_I, _D]
+        L.oracle_central_lapse.restype = ctypes.c_double
+        L.oracle_compaction.argtypes = G + [_D, ctypes.c_int, _D]
+        L.oracle_compaction_vjp.argtypes = G + [_D, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
+        L._diag_sigs = True
+    return L
+
+
+def _zeta_array(g: OGrid, zeta):
+    z = np.ascontiguousarray(np.asarray(zeta, dtype=np.float64).reshape(g.n[2], g.n[1], g.n[0]))
+    return z
+
+
+def init_zeta(g: OGrid, params, zeta, a0=1.0):
+    """FLRW + curvature-perturbation data at leading gradient order from a per-point
+    zeta [nz, ny, nx] (the paper's initial-data paragraph; fluid at rest, E from the
+    discrete Hamiltonian constraint)."""
+    z = _zeta_array(g, zeta)
+    state = np.empty((nfields(params), g.n[2], g.n[1], g.n[0]), dtype=np.float64)
+    n, h, x0 = g.c()
+    _diag_lib().oracle_init_zeta(n, h, x0, _dp(params), _dp(z), float(a0), _dp(state))
+    return state
+
+
+def init_zeta_vjp(g: OGrid, params, zeta, lam0, a0=1.0):
+    """zeta_bar = (d init_zeta / d zeta)^T lam0 by a tape (tiny grids)."""
+    z = _zeta_array(g, zeta)
+    lam0 = np.ascontiguousarray(lam0, dtype=np.float64)
+    assert lam0.shape == (nfields(params), g.n[2], g.n[1], g.n[0])
+    out = np.empty_like(z)
+    n, h, x0 = g.c()
+    _diag_lib().oracle_init_zeta_vjp(n, h, x0, _dp(params), _dp(z), float(a0), _dp(lam0), _dp(out))
+    return out
+
+
+def central_lapse(g: OGrid, state):
+    """alpha at the centre grid point (nx/2, ny/2, nz/2)."""
+    n, _, _ = g.c()
+    return float(_diag_lib().oracle_central_lapse(n, _dp(np.ascontiguousarray(state))))
+
+
+def compaction(g: OGrid, params, state, kmax):
+    """C(r_k) = 2 dM(r_k) / R(r_k) for k = 1..kmax about the centre point (array [kmax])."""
+    _check_state(g, params, state)
+    out = np.empty(int(kmax), dtype=np.float64)
+    n, h, x0 = g.c()
+    _diag_lib().oracle_compaction(n, h, x0, _dp(params), _dp(state), int(kmax), _dp(out))
+    return out
+
+
+def compaction_vjp(g: OGrid, params, state, kmax, kstar, cbar=1.0):
+    """cbar d C(r_kstar) / d state, state layout, by a tape."""
+    _check_state(g, params, state)
+    out = np.empty_like(state)
+    n, h, x0 = g.c()
+    _diag_lib().oracle_compaction_vjp(n, h, x0, _dp(params), _dp(state), int(kmax), int(kstar), float(cbar),
+                                      _dp(out))
+    return out
+
+
+def collapse_run(g: OGrid, params, zeta, dt, steps, kmax, a0=1.0):
+    """Forward pipeline: init_zeta, `steps` RK4 steps from t = 0.  Returns a dict with
+    every time level (`states`), the central lapse per level (`alphas`), the first
+    level attaining its minimum (`nstar`), the final compaction function (`C`) and the
+    first maximising radius index (`kstar`, 1-based)."""
+    U = init_zeta(g, params, zeta, a0)
+    states = [U.copy()]
+    alphas = [central_lapse(g, U)]
+    for s in range(steps):
+        rk4_step(g, params, U, s * dt, dt)
+        states.append(U.copy())
+        alphas.append(central_lapse(g, U))
+    C = compaction(g, params, U, kmax)
+    alphas = np.array(alphas)
+    return dict(states=states, alphas=alphas, nstar=int(np.argmin(alphas)), min_lapse=float(alphas.min()),
+                C=C, kstar=int(np.argmax(C)) + 1, peak=float(C.max()))
+
+
+def collapse_gradient(g: OGrid, params, zeta, dt, steps, kmax, a0=1.0, run=None):
+    """(d min-central-lapse / d zeta, d peak-compaction / d zeta), each [nz, ny, nx]:
+    the compaction's tape at the final level, the lapse seed at the first minimising
+    level, the RK4 adjoint step (tape of the right-hand side) back through every level,
+    then the tape of the zeta map.  Tiny grids only."""
+    r = run if run is not None else collapse_run(g, params, zeta, dt, steps, kmax, a0)
+    ia = ALPHA_FIELD
+    nz, ny, nx = g.n[2], g.n[1], g.n[0]
+    out = []
+    for which in ("lapse", "compaction"):
+        if which == "compaction":
+            lam = compaction_vjp(g, params, r["states"][steps], kmax, r["kstar"])
+        else:
+            lam = np.zeros_like(r["states"][0])
+        if which == "lapse" and r["nstar"] == steps:
+            lam[ia, nz // 2, ny // 2, nx // 2] += 1.0
+        for s in reversed(range(steps)):
+            lam = adjoint_step(g, params, r["states"][s], lam, s * dt, dt)
+            if which == "lapse" and s == r["nstar"]:
+                lam[ia, nz // 2, ny // 2, nx // 2] += 1.0
+        out.append(init_zeta_vjp(g, params, zeta, lam, a0))
+    return out[0], out[1], r
+
+
+ALPHA_FIELD = 17

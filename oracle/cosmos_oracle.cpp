@@ -20,8 +20,8 @@
  *     perturbation zeta, the fluid density fixed so that the (discrete)
  *     Hamiltonian constraint holds (section "Physical system settings", last
  *     paragraph).
- * The paper does not print these formulas; the readings taken for every
- * silent point are listed in the repository's design notes.
+ * The paper does not print these formulas; each reading taken where it is
+ * silent is stated beside the code that takes it.
  *
  * Style: full 3x3 index arrays and explicit loops over the summed indices, in
  * the textbook notation; no blocking, no fusion, no reuse beyond named
@@ -74,6 +74,7 @@ inline double val(Cnt a) { return a.v; }
 inline double val(double a) { return a; }
 using std::sqrt;
 using std::fabs;
+using std::exp;
 
 /* ------------------------------------------------------------------------ */
 /* Taped scalar for reverse mode: every operation appends a node holding its */
@@ -105,6 +106,29 @@ inline AD sqrt(AD x) {
   return node(r, x.id, 0.5 / r);
 }
 inline AD fabs(AD x) { return node(std::fabs(x.v), x.id, x.v < 0.0 ? -1.0 : 1.0); }
+inline AD exp(AD x) {
+  double e = std::exp(x.v);
+  return node(e, x.id, e);
+}
+inline double val(AD a) { return a.v; }
+inline long tape_id(double) { return -1; }
+inline long tape_id(AD a) { return a.id; }
+
+/* Adjoints of the first nleaves tape entries after one reverse sweep from the
+ * given (node id, cotangent) seeds. */
+std::vector<double> reverse_sweep(long nleaves, const std::vector<std::pair<long, double>>& seeds) {
+  std::vector<double> adj(g_tape.size(), 0.0);
+  for (auto& sd : seeds) adj[sd.first] += sd.second;
+  for (long q = (long)g_tape.size() - 1; q >= nleaves; --q) {
+    const double a = adj[q];
+    if (a == 0.0) continue;
+    const TapeNode& nd = g_tape[q];
+    if (nd.a >= 0) adj[nd.a] += a * nd.da;
+    if (nd.b >= 0) adj[nd.b] += a * nd.db;
+  }
+  adj.resize(nleaves);
+  return adj;
+}
 inline bool operator<(AD x, AD y) { return x.v < y.v; }
 inline bool operator>(AD x, AD y) { return x.v > y.v; }
 
@@ -207,6 +231,9 @@ inline long wrapi(long a, long n) {
 struct Field {
   const Grid* g;
   const double* s;
+  // reverse mode only: tape id of every entry (-1 = constant); when null the
+  // entries themselves are the tape's leaves (id = their index)
+  const long* ids = nullptr;
   long wrapped(int d, long a) const {
     long m = a + WRAP_PAD;
     if (m >= 0 && m < (long)g->wrap[d].size()) return g->wrap[d][m];
@@ -221,7 +248,10 @@ struct Field {
 
 /* A state entry as a value of the scalar type (a tape leaf for reverse mode). */
 template <class R> inline R load(const Field& F, int f, Pt p) { return R(F.at(f, p)); }
-template <> inline AD load<AD>(const Field& F, int f, Pt p) { return AD(F.at(f, p), F.index(f, p)); }
+template <> inline AD load<AD>(const Field& F, int f, Pt p) {
+  const long q = F.index(f, p);
+  return AD(F.s[q], F.ids ? F.ids[q] : q);
+}
 
 inline Pt shift(Pt p, int d, long o) {
   p.i[d] += o;
@@ -1367,6 +1397,108 @@ void fmr_init(const Hier& H, const Params& P, const double* id, double* const* U
 
 }  // namespace
 
+/* ------------------------------------------------------------------------ */
+/* Collapse diagnostics and initial data from a per-point zeta: the        */
+/* quantities a threshold search differentiates (the paper's PBH examples  */
+/* follow the lapse at the centre and the compaction of the overdensity,   */
+/* section "Examples"; it defines neither).  Readings taken here:           */
+/*  - zeta map: the leading-order FLRW + curvature-perturbation data of     */
+/*    init_all kind 1 with zeta given at every grid point instead of the    */
+/*    Gaussian: chi = exp(-2 zeta)/a0^2, gt = delta, K = -3 H0, At = 0,     */
+/*    Gt = 0, alpha = 1, beta = B = 0, fluid at rest, E from the discrete   */
+/*    Hamiltonian constraint, tau~ = E chi^{-3/2} (section "Physical system */
+/*    settings", initial-data paragraph);                                   */
+/*  - central lapse: alpha at the grid point c = (nx/2, ny/2, nz/2); its    */
+/*    minimum over the time levels t_0 .. t_N of a run;                     */
+/*  - compaction function about c on a grid of equal spacing h:             */
+/*      C(r_k) = 2 dM(r_k) / R(r_k),  r_k = k h,  k = 1 .. kmax,            */
+/*      dM(r_k) = h^3 sum over the points with |x - c| < r_k of             */
+/*                (tau~ - Ebar sqrt(gamma)),  sqrt(gamma) = chi^{-3/2},     */
+/*      Ebar = (box sum of tau~) / (box sum of sqrt(gamma)): the volume-    */
+/*             weighted mean energy density, so dM is the mass excess;      */
+/*      R(r_k) = r_k times the mean of chi^{-1/2} over the six grid points  */
+/*             on the axes through c at distance r_k (the areal radius of   */
+/*             the conformally flat metric delta/chi);                      */
+/*    |x - c| < r_k is decided in integers: di^2 + dj^2 + dk^2 < k^2;       */
+/*    the peak compaction is the largest C(r_k).                            */
+/* The reverse modes are tapes over these same templated functions.         */
+/* ------------------------------------------------------------------------ */
+template <class R>
+void init_zeta(const Grid& g, const Params& P, const R* zeta, double a0, std::vector<R>& st) {
+  const long N = g.npts();
+  const int nf = P.nf();
+  st.assign((size_t)nf * N, R(0.0));
+  for (long m = 0; m < N; ++m) {
+    st[CHI * N + m] = exp(R(-2.0) * zeta[m]) / R(a0 * a0);
+    st[(GT + 0) * N + m] = R(1.0);
+    st[(GT + 3) * N + m] = R(1.0);
+    st[(GT + 5) * N + m] = R(1.0);
+    st[TRK * N + m] = R(-3.0 * P.H0);
+    st[ALP * N + m] = R(1.0);
+  }
+  if (!P.fluid) return;
+  // E from the discrete Hamiltonian constraint of the metric just set
+  std::vector<double> v((size_t)nf * N);
+  std::vector<long> ids((size_t)nf * N);
+  for (size_t q = 0; q < v.size(); ++q) {
+    v[q] = val(st[q]);
+    ids[q] = tape_id(st[q]);
+  }
+  Field F{&g, v.data(), is_ad<R>::value ? ids.data() : nullptr};
+  Params Pv = P;
+  Pv.fluid = 0;
+  Pv.scalar = 0;
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        Pt p{{i, j, k}};
+        Local<R> L;
+        gather<R>(F, Pv, p, L);
+        Geom<R> G;
+        geometry<R>(L, G);
+        R E = (G.Rs + R(2.0 / 3.0) * L.K * L.K - G.AA) / R(16.0 * PI);
+        st[(long)P.ifl() * N + (k * g.n[1] + j) * g.n[0] + i] = E / (L.chi * sqrt(L.chi));
+      }
+}
+
+template <class R>
+void compaction(const Grid& g, const Params& P, const Field& F, int kmax, R* C) {
+  const long c[3] = {g.n[0] / 2, g.n[1] / 2, g.n[2] / 2};
+  const double h = g.h[0];
+  const int q = P.ifl();
+  R St = R(0.0), Sg = R(0.0);
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        Pt p{{i, j, k}};
+        R chi = load<R>(F, CHI, p);
+        St = St + load<R>(F, q, p);
+        Sg = Sg + R(1.0) / (chi * sqrt(chi));
+      }
+  R Ebar = St / Sg;
+  for (int kk = 1; kk <= kmax; ++kk) {
+    R dM = R(0.0);
+    for (long k = 0; k < g.n[2]; ++k)
+      for (long j = 0; j < g.n[1]; ++j)
+        for (long i = 0; i < g.n[0]; ++i) {
+          const long di = i - c[0], dj = j - c[1], dk = k - c[2];
+          if (di * di + dj * dj + dk * dk >= (long)kk * kk) continue;
+          Pt p{{i, j, k}};
+          R chi = load<R>(F, CHI, p);
+          dM = dM + (load<R>(F, q, p) - Ebar / (chi * sqrt(chi)));
+        }
+    R s6 = R(0.0);
+    for (int d = 0; d < 3; ++d)
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        Pt p{{c[0], c[1], c[2]}};
+        p.i[d] += sgn * kk;
+        s6 = s6 + R(1.0) / sqrt(load<R>(F, CHI, p));
+      }
+    R Rk = R(kk * h) * (s6 / R(6.0));
+    C[kk - 1] = R(2.0 * h * h * h) * dM / Rk;
+  }
+}
+
 /* ======================================================================== */
 /* C API (ctypes)                                                            */
 /*   n[3] grid points, h[3] spacings, x0[3] coordinate of point 0,           */
@@ -1618,6 +1750,76 @@ void oracle_fmr_restrict(int L, const int* n, const double* h, const double* x0,
 void oracle_rk4_dense(long M, const double* Un, const double* k, double dt, double theta, double* out) {
   const double* ks[4] = {k, k + M, k + 2 * M, k + 3 * M};
   rk4_dense(M, Un, ks, dt, theta, out);
+}
+
+
+/* Initial data from a per-point zeta (one value per point, [k][j][i]); see
+ * the collapse-diagnostics section for the map. */
+void oracle_init_zeta(const int* n, const double* h, const double* x0, const double* params, const double* zeta,
+                      double a0, double* state) {
+  Grid g = make_grid(n, h, x0);
+  Params P = unpack_params(params);
+  std::vector<double> st;
+  init_zeta<double>(g, P, zeta, a0, st);
+  std::memcpy(state, st.data(), sizeof(double) * st.size());
+}
+
+/* zeta_bar = (d state0 / d zeta)^T lam0 for the map of oracle_init_zeta, by a
+ * tape whose leaves are the zeta values.  Single-threaded; tiny grids. */
+void oracle_init_zeta_vjp(const int* n, const double* h, const double* x0, const double* params,
+                          const double* zeta, double a0, const double* lam0, double* zeta_bar) {
+  Grid g = make_grid(n, h, x0);
+  Params P = unpack_params(params);
+  const long N = g.npts();
+  g_tape.clear();
+  std::vector<AD> z(N);
+  for (long m = 0; m < N; ++m) {
+    g_tape.push_back(TapeNode{-1, -1, 0.0, 0.0});
+    z[m] = AD(zeta[m], m);
+  }
+  std::vector<AD> st;
+  init_zeta<AD>(g, P, z.data(), a0, st);
+  std::vector<std::pair<long, double>> seeds;
+  for (size_t q = 0; q < st.size(); ++q)
+    if (st[q].id >= 0) seeds.push_back({st[q].id, lam0[q]});
+  std::vector<double> adj = reverse_sweep(N, seeds);
+  for (long m = 0; m < N; ++m) zeta_bar[m] = adj[m];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+}
+
+/* alpha at the centre grid point (nx/2, ny/2, nz/2). */
+double oracle_central_lapse(const int* n, const double* state) {
+  const long N = (long)n[0] * n[1] * n[2];
+  return state[ALP * N + ((long)(n[2] / 2) * n[1] + n[1] / 2) * n[0] + n[0] / 2];
+}
+
+/* Compaction C(r_k), k = 1..kmax, into C[kmax] (equal spacing; fluid on). */
+void oracle_compaction(const int* n, const double* h, const double* x0, const double* params, const double* state,
+                       int kmax, double* C) {
+  Grid g = make_grid(n, h, x0);
+  Field F{&g, state};
+  compaction<double>(g, unpack_params(params), F, kmax, C);
+}
+
+/* lam = cbar d C(r_kstar) / d state (state layout), by a tape over the same
+ * function whose leaves are the state entries. */
+void oracle_compaction_vjp(const int* n, const double* h, const double* x0, const double* params,
+                           const double* state, int kmax, int kstar, double cbar, double* lam) {
+  Grid g = make_grid(n, h, x0);
+  Params P = unpack_params(params);
+  Field F{&g, state};
+  const long M = (long)P.nf() * g.npts();
+  g_tape.clear();
+  for (long m = 0; m < M; ++m) g_tape.push_back(TapeNode{-1, -1, 0.0, 0.0});
+  std::vector<AD> C(kmax);
+  compaction<AD>(g, P, F, kmax, C.data());
+  std::vector<std::pair<long, double>> seeds;
+  if (C[kstar - 1].id >= 0) seeds.push_back({C[kstar - 1].id, cbar});
+  std::vector<double> adj = reverse_sweep(M, seeds);
+  for (long m = 0; m < M; ++m) lam[m] = adj[m];
+  g_tape.clear();
+  g_tape.shrink_to_fit();
 }
 
 }  // extern "C"

@@ -25,9 +25,6 @@ import torch
 
 from . import cosmos as C
 
-ALPHA = 17
-
-
 def _ws(nbytes, device):
     return torch.empty((nbytes + 7) // 8, dtype=torch.float64, device=device) if nbytes else None
 
@@ -46,7 +43,6 @@ class CollapseRun:
         self.device = torch.device(device)
         self.nf = C.cosmos_nfields(params)
         self.fs = C.cosmos_field_stride(self.g)
-        self.centre = ((n // 2) * n + n // 2) * n + n // 2  # (k, j, i) = (n/2, n/2, n/2), pitch = n
         dev = self.device
         self.ws_rk4 = _ws(C.cosmos_workspace_bytes(self.g, params, C.COSMOS_OP_RK4), dev)
         self.ws_init = _ws(C.cosmos_workspace_bytes(self.g, params, C.COSMOS_OP_INIT), dev)
@@ -74,19 +70,21 @@ class CollapseRun:
         self.init(zeta, U)
         U0 = U.clone()
         alphas = torch.empty(self.steps + 1, dtype=torch.float64, device=self.device)
-        alphas[0] = U[ALPHA * self.fs + self.centre]
+        C.check(C.cosmos_central_lapse(self.g, self.p, U, alphas, 0))
         checkpoints = {0: U.clone()}
         for s in range(self.steps):
             self.step(U, s)
-            alphas[s + 1] = U[ALPHA * self.fs + self.centre]
+            C.check(C.cosmos_central_lapse(self.g, self.p, U, alphas, s + 1))
             if (s + 1) % self.every == 0 and s + 1 < self.steps:
                 checkpoints[s + 1] = U.clone()
-        a = alphas.cpu()
-        nstar = int(torch.argmin(a))
+        res = torch.empty(2, dtype=torch.float64, device=self.device)
+        C.check(C.cosmos_series_argmin(alphas, self.steps + 1, res))
+        amin, nstar = res.cpu().tolist()
+        nstar = int(nstar)
         Ck, aux = self.compaction(U)
-        kstar = max(range(len(Ck)), key=lambda k: Ck[k]) + 1
-        rec = dict(U0=U0, final=U, checkpoints=checkpoints, nstar=nstar, kstar=kstar, aux=aux)
-        return float(a[nstar]), float(Ck[kstar - 1]), rec
+        kstar = max(range(len(Ck)), key=lambda k: Ck[k]) + 1  # first maximising radius (host values)
+        rec = dict(U0=U0, final=U, checkpoints=checkpoints, nstar=nstar, kstar=kstar, aux=aux, alphas=alphas)
+        return amin, float(Ck[kstar - 1]), rec
 
     def backward(self, rec, gbar_alpha, gbar_comp):
         """zeta_bar for the cotangents of (min lapse, peak compaction)."""
@@ -94,7 +92,7 @@ class CollapseRun:
         C.check(C.cosmos_compaction_vjp(self.g, self.p, rec["final"], rec["kstar"], self.kmax, rec["aux"],
                                         float(gbar_comp), lam))
         if rec["nstar"] == self.steps:
-            lam[ALPHA * self.fs + self.centre] += gbar_alpha
+            C.check(C.cosmos_central_lapse_vjp(self.g, self.p, gbar_alpha, lam))
         starts = sorted(rec["checkpoints"].keys())
         for si in reversed(range(len(starts))):
             s0 = starts[si]
@@ -111,7 +109,7 @@ class CollapseRun:
                 C.check(C.cosmos_adjoint_step_stages(self.g, self.p, Un, U2, U3, U4, lam, lam, s * self.dt, self.dt,
                                                      self.ws_adj))
                 if s == rec["nstar"]:
-                    lam[ALPHA * self.fs + self.centre] += gbar_alpha
+                    C.check(C.cosmos_central_lapse_vjp(self.g, self.p, gbar_alpha, lam))
             del saved
         zbar = torch.empty(self.fs, dtype=torch.float64, device=self.device)
         C.check(C.cosmos_init_zeta_vjp(self.g, self.p, rec["U0"], lam, zbar, self.ws_ivjp))

@@ -103,6 +103,9 @@ _SIGS = {
                            ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_compaction_vjp": ([_G, _PP, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _D, _P, _P],
                               ctypes.c_int),
+    "cosmos_central_lapse": ([_G, _PP, _P, _P, ctypes.c_int, _P], ctypes.c_int),
+    "cosmos_central_lapse_vjp": ([_G, _PP, _D, _P, _P], ctypes.c_int),
+    "cosmos_series_argmin": ([_P, ctypes.c_int, _P, _P], ctypes.c_int),
     "cosmos_batch_workspace_bytes": ([ctypes.c_int, _G, _PP, ctypes.c_int], ctypes.c_size_t),
     "cosmos_batch_plan": ([ctypes.c_int, _G, _PP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(cosmos_batch_tuning), _P, _S,
@@ -321,6 +324,19 @@ def cosmos_compaction(g, p, state, kmax, ws=None, stream=None):
 def cosmos_compaction_vjp(g, p, state, kstar, kmax, aux, cbar, lam, stream=None) -> int:
     return lib().cosmos_compaction_vjp(ctypes.byref(g), ctypes.byref(p), _ptr(state), int(kstar), int(kmax), aux,
                                        float(cbar), _ptr(lam), _stream(stream))
+
+
+def cosmos_central_lapse(g, p, state, series, index, stream=None) -> int:
+    return lib().cosmos_central_lapse(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(series), int(index),
+                                      _stream(stream))
+
+
+def cosmos_central_lapse_vjp(g, p, abar, lam, stream=None) -> int:
+    return lib().cosmos_central_lapse_vjp(ctypes.byref(g), ctypes.byref(p), float(abar), _ptr(lam), _stream(stream))
+
+
+def cosmos_series_argmin(series, count, result, stream=None) -> int:
+    return lib().cosmos_series_argmin(_ptr(series), int(count), _ptr(result), _stream(stream))
 
 
 def cosmos_batch_workspace_bytes(grids, p, max_steps) -> int:

@@ -12,6 +12,8 @@
 
 namespace cosmos {
 
+constexpr int kAlphaField = 17;  // the lapse's place in the state's field order
+
 static size_t a256(size_t doubles) { return ((doubles * 8 + 255) & ~(size_t)255) / 8; }
 
 struct AdjLayout {
@@ -281,6 +283,45 @@ __global__ void compaction_vjp_kernel(const CompVjp q, const double* __restrict_
   lam[24 * fs + c] = tau_bar;
 }
 
+// Central lapse of one time level: series[index] = alpha at the centre point.
+__global__ void central_lapse_kernel(const double* __restrict__ U, long idx, double* __restrict__ series, int index) {
+  series[index] = U[idx];
+}
+
+// Reverse of the central-lapse read: lam[idx] += abar.
+__global__ void central_lapse_vjp_kernel(double* __restrict__ lam, long idx, double abar) { lam[idx] += abar; }
+
+// (minimum, first index attaining it) of v[0 .. count-1] by one warp: lane l
+// scans l, l + 32, ... keeping the first strict minimum, then the lanes are
+// merged pairwise preferring the smaller value and, on equal values, the
+// smaller index.  A NaN never wins against a number.  Deterministic.
+__global__ void series_argmin_kernel(const double* __restrict__ v, int count, double* __restrict__ out) {
+  const int lane = threadIdx.x;
+  double best = NAN;
+  int bi = count;  // "none yet"
+  for (int q = lane; q < count; q += 32) {
+    const double x = v[q];
+    if (bi == count || x < best || (isnan(best) && !isnan(x))) {
+      best = x;
+      bi = q;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    const bool take = oi < count && (bi == count || ob < best || (ob == best && oi < bi) ||
+                                     (isnan(best) && !isnan(ob)) || (isnan(best) && isnan(ob) && oi < bi));
+    if (take) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    out[0] = best;
+    out[1] = (double)bi;
+  }
+}
+
 __global__ void init_zeta_metric(const DevGrid g, const double* __restrict__ zeta, double a0, double H0, int nf,
                                  double* __restrict__ U) {
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -496,6 +537,31 @@ int cosmos_compaction(const cosmos_grid* g, const cosmos_params* p, const double
   aux_host[4 * kmax + 0] = S_all;
   aux_host[4 * kmax + 1] = V_all;
   return COSMOS_OK;
+}
+
+int cosmos_central_lapse(const cosmos_grid* g, const cosmos_params* p, const double* state, double* series,
+                         int index, void* stream) {
+  int e = check_adj(g, p);
+  if (e) return e;
+  if (!state || !series || index < 0) return COSMOS_EINVAL;
+  const long idx = (long)kAlphaField * cosmos_field_stride(g) + ((long)(g->nz / 2) * g->ny + g->ny / 2) * g->pitch + g->nx / 2;
+  central_lapse_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(state, idx, series, index);
+  return cudaGetLastError() == cudaSuccess ? COSMOS_OK : COSMOS_ECUDA;
+}
+
+int cosmos_central_lapse_vjp(const cosmos_grid* g, const cosmos_params* p, double abar, double* lam, void* stream) {
+  int e = check_adj(g, p);
+  if (e) return e;
+  if (!lam) return COSMOS_EINVAL;
+  const long idx = (long)kAlphaField * cosmos_field_stride(g) + ((long)(g->nz / 2) * g->ny + g->ny / 2) * g->pitch + g->nx / 2;
+  central_lapse_vjp_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(lam, idx, abar);
+  return cudaGetLastError() == cudaSuccess ? COSMOS_OK : COSMOS_ECUDA;
+}
+
+int cosmos_series_argmin(const double* series, int count, double* result, void* stream) {
+  if (!series || !result || count < 1) return COSMOS_EINVAL;
+  series_argmin_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(series, count, result);
+  return cudaGetLastError() == cudaSuccess ? COSMOS_OK : COSMOS_ECUDA;
 }
 
 int cosmos_compaction_vjp(const cosmos_grid* g, const cosmos_params* p, const double* state, int kstar, int kmax,
