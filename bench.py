@@ -107,6 +107,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=N_GRID, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-extras", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "scan", "adjoint", "flrw", "fmr", "isocurvature", "mode"],
                     help="sweep: single 256^3 grid (headline); scan: 64-instance batched threshold scan; "
@@ -363,32 +364,21 @@ def fmr_workload(args):
     print(json.dumps(line), flush=True)
 
 
-def scan_workload(args):
-    """Batched threshold scan: 64 FLRW + zeta instances on uneven 64^3..96^3 grids
-    (radiation fluid w = 1/3, H0 L = 40, mu, sigma, axis ratios from SplitMix64
-    seed 2606), dt = h/4 per instance.  Times the batched CUDA-graph run against
-    the plain per-instance loop (cosmos_rk4_step per grid) on the same GPU, over
-    the same steps, and checks that both give the same states."""
+def measure_scan(n_instances, K, W, rank=0, world=1, autotune=True):
+    """Batched threshold scan against the plain per-instance loop: `n_instances` FLRW +
+    zeta instances on uneven 64^3..96^3 grids (radiation fluid w = 1/3, H0 L = 40, mu,
+    sigma, axis ratios from SplitMix64 seed 2606), dt = h/4 per instance.  The batch
+    runs W warm-up and K timed steps as one CUDA graph; the loop (cosmos_rk4_step per
+    grid) runs the same steps from the same states; both end in the same states."""
     import torch
 
-    from paper_2606_02053_gb300 import build, inputs
+    from paper_2606_02053_gb300 import inputs
     from paper_2606_02053_gb300 import cosmos as C
     from paper_2606_02053_gb300.batch import BatchScan
-
     from paper_2606_02053_gb300.dist import max_over_ranks, shard_instances, sum_over_ranks
 
-    ws_, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    if ws_ > 1:
-        import torch.distributed as tdist
-
-        tdist.init_process_group("nccl")
-    if rank == 0:
-        build.build()
-    if ws_ > 1:
-        tdist.barrier()
-    inst_all = inputs.scan_instances(args.instances, seed=2606)
-    mine = shard_instances([d["n"] ** 3 for d in inst_all], ws_)[rank]
+    inst_all = inputs.scan_instances(n_instances, seed=2606)
+    mine = shard_instances([d["n"] ** 3 for d in inst_all], world)[rank]
     inst = [inst_all[i] for i in mine]
     p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
     grids, dts, ids = [], [], []
@@ -399,11 +389,10 @@ def scan_workload(args):
         dts.append(0.25 * h)
         ids.append(C.make_id(1, mu=d["mu"], sigma=d["sigma"], q=d["q"]))
     total_pts = float(sum(g.nx * g.ny * g.nz for g in grids))
-    K, W = args.steps, args.warmup
     b = BatchScan(grids, p, dts, max_steps=W + K)
     b.init(ids)
     init_states = [s.clone() for s in b.states]
-    tune = b.autotune(reps=2)
+    tune = b.autotune(reps=2) if autotune else None
     stream = torch.cuda.Stream()
     b.run(0, W, use_graph=True, stream=stream)
     torch.cuda.synchronize()
@@ -431,20 +420,48 @@ def scan_workload(args):
     torch.cuda.synchronize()
     t_loop = max_over_ranks(f0.elapsed_time(f1) * 1e-3)
     max_diff = max_over_ranks(max(float((a - c).abs().max()) for a, c in zip(b.states, loop_states)))
+    scale = max(float(a.abs().max()) for a in loop_states)
     total_pts = sum_over_ranks(total_pts)
-    value = total_pts * K / t_batch
+    del b, init_states, loop_states, ws
+    torch.cuda.empty_cache()
+    return {"instances": len(inst_all), "grid_sizes": [d["n"] for d in inst_all], "points_total": int(total_pts),
+            "steps_timed": K, "warmup": W, "value": total_pts * K / t_batch,
+            "per_instance_loop_value": total_pts * K / t_loop, "speedup": t_loop / t_batch,
+            "ms_per_step": 1e3 * t_batch / K, "loop_ms_per_step": 1e3 * t_loop / K,
+            "max_abs_diff_vs_loop": max_diff, "max_rel_diff_vs_loop": max_diff / scale, "autotune": tune,
+            "gpu_launches": K * 4 * 6}  # per stage: primitives, fluxes, exponents, limbs, derivative, algebra
+
+
+def scan_workload(args):
+    """The batched threshold scan as its own line (150 steps by default)."""
+    import torch
+
+    from paper_2606_02053_gb300 import build
+
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws_ > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    if rank == 0:
+        build.build()
+    if ws_ > 1:
+        tdist.barrier()
+    r = measure_scan(args.instances, args.steps, args.warmup, rank, ws_)
     if rank != 0:
         return
-    line = {"metric": f"batched threshold-scan FP64 grid-point RK4 updates/sec ({len(inst_all)} instances, "
-                      f"{min(d['n'] for d in inst_all)}^3-{max(d['n'] for d in inst_all)}^3)",
-            "value": value, "unit": UNIT, "steps": K, "warmup": W,
-            "ms_per_step": 1e3 * t_batch / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+    line = {"metric": f"batched threshold-scan FP64 grid-point RK4 updates/sec ({r['instances']} instances, "
+                      f"{min(r['grid_sizes'])}^3-{max(r['grid_sizes'])}^3)",
+            "value": r["value"], "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "n_gpus": ws_,
-            "config": {"workload": f"flrw_zeta_scan_{len(inst_all)}_instances_fluid_w1/3", "instances": len(inst_all),
-                       "points_total": int(total_pts), "grid_sizes": [d["n"] for d in inst_all]},
-            "per_instance_loop_value": total_pts * K / t_loop, "batched_speedup": t_loop / t_batch,
-            "batched_vs_loop_max_abs_diff": max_diff, "autotune": tune,
-            "gpu_launches": K * 4 * 6}  # per stage: primitives, fluxes, exponents, limbs, derivative, algebra
+            "config": {"workload": f"flrw_zeta_scan_{r['instances']}_instances_fluid_w1/3",
+                       "instances": r["instances"], "points_total": r["points_total"],
+                       "grid_sizes": r["grid_sizes"]},
+            "per_instance_loop_value": r["per_instance_loop_value"], "batched_speedup": r["speedup"],
+            "batched_vs_loop_max_abs_diff": r["max_abs_diff_vs_loop"], "autotune": r["autotune"],
+            "gpu_launches": r["gpu_launches"]}
     print(json.dumps(line), flush=True)
 
 
@@ -499,18 +516,43 @@ def dist_env():
 
 
 def reference_arm(args):
-    """The oracle (plain FP64 CPU code) timed on the host cores, same metric."""
+    """The oracle (plain FP64 CPU code) timed on the host cores, same metric.  One step
+    evaluates the four right-hand sides of an RK4 step on a slab of `planes` z-planes of
+    the 256^3 gauge-wave state (the oracle cannot step the whole grid in a bench run):
+    the timed region really takes ms_per_step x steps, and value = points updated / s."""
+    import oracle as O
+
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    res = cpu_baseline_sample(args.grid, planes=16, repeats=max(1, args.steps), warmups=args.warmup)
-    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds_per_step"], "higher_is_better": True,
+    n, planes = args.grid, 8
+    O.set_threads(os.cpu_count() or 1)
+    h = 1.0 / n
+    op = O.params_array(slicing=0, shift=1, eta=2.0, ko_sigma=0.1)
+    og = O.OGrid((n, n, n), h)
+    state = O.init(og, op, O.id_array(0, A=0.01))
+
+    def step():
+        for _ in range(4):
+            O.rhs_planes(og, op, state, 0, planes)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    elapsed = time.perf_counter() - t0
+    value = planes * n * n * args.steps / elapsed
+    sample = (f"oracle: the 4 right-hand sides of an RK4 step on {planes} of {n} z-planes ({planes * n * n} points) "
+              f"per step, {args.steps} steps after {args.warmup} warm-up; host threads {O.max_threads()}")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "grid": args.grid, "fields": STATE_FIELDS},
-            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
-                             "sample": res["sample"]},
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD, "grid": n, "fields": STATE_FIELDS,
+                       "sampled": f"each step updates {planes} of the {n} z-planes; the rate is per point"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -551,25 +593,23 @@ def cpu_baseline_sample(n, planes, repeats=1, state=None, warmups=0):
             "flops": counts, "flops_parts": parts}
 
 
-def adjoint_workload(args):
-    """96^3 FLRW + Gaussian zeta (mu = 0.6, sigma = L/8, radiation fluid, H0 L = 40),
-    256 RK4 steps (dt = h/4), checkpoints every 16 steps.  Gradients of the minimum
-    central lapse and of the peak compaction with respect to mu and to zeta at every
-    point, by the adjoint; checked with central differences (h = 1e-6) on mu, on 8
-    random points and on 2 random directions of zeta.  The adjoint's cost is set
-    against the finite-difference loop (2 forward runs per scalar)."""
+def measure_adjoint(n, steps, every=16, point_checks=True):
+    """FLRW + Gaussian zeta on n^3 (mu = 0.6, sigma = L/8, radiation fluid, H0 L = 40),
+    `steps` RK4 steps (dt = h/4), checkpoints every `every` steps.  Gradients of the
+    minimum central lapse and of the peak compaction with respect to mu and to zeta at
+    every point, by the adjoint; checked with central differences (h = 1e-6) along mu
+    and, with point_checks, on 8 random points and 2 random directions of zeta.  The
+    adjoint's cost is set against the plain finite-difference loop (2 forward runs per
+    scalar), whose forward run is timed here."""
     import numpy as np
     import torch
 
-    from paper_2606_02053_gb300 import build
     from paper_2606_02053_gb300 import cosmos as C
     from paper_2606_02053_gb300.adjoint import CollapseRun, CosmosAdjoint
 
-    build.build()
-    n, steps = args.adjoint_grid, args.adjoint_steps
     h = 1.0 / n
     p = C.make_params(slicing=0, shift=1, fluid=1, w=1.0 / 3.0, H0=40.0)
-    run = CollapseRun(n, p, dt=0.25 * h, steps=steps, checkpoint_every=16)
+    run = CollapseRun(n, p, dt=0.25 * h, steps=steps, checkpoint_every=every)
     x = (-(n // 2) + torch.arange(n, dtype=torch.float64, device="cuda")) * h
     Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
     shape = torch.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * (1.0 / 8.0) ** 2)).reshape(-1).contiguous()
@@ -585,59 +625,82 @@ def adjoint_workload(args):
     run.forward(mu0 * shape)  # warm-up
     mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
     zeta = (mu * shape).contiguous()
-    zeta.retain_grad()
     out, t_fwd = timed(lambda: CosmosAdjoint.apply(zeta, run))
-    (g_mu_min,), t_b1 = timed(lambda: torch.autograd.grad(out[0], mu, retain_graph=True))
+    (g_mu_min,), _ = timed(lambda: torch.autograd.grad(out[0], mu, retain_graph=True))
     # per-point gradients of each diagnostic (one reverse run each)
     amin, cpeak, rec = run.forward((mu0 * shape).contiguous())
     zb_min, t_bmin = timed(lambda: run.backward(rec, 1.0, 0.0))
     zb_comp, t_bcomp = timed(lambda: run.backward(rec, 0.0, 1.0))
     g_mu_comp = float(torch.dot(zb_comp, shape))
-    g_mu_min_v = float(g_mu_min)
     hfd = 1e-6
     checks = []
 
     def fd(direction, label):
         zp = (mu0 * shape + hfd * direction).contiguous()
         zm = (mu0 * shape - hfd * direction).contiguous()
-        a1, c1, _ = run.forward(zp)
+        (a1, c1, _), t1 = timed(lambda: run.forward(zp))
         a2, c2, _ = run.forward(zm)
         fmin, fcomp = (a1 - a2) / (2 * hfd), (c1 - c2) / (2 * hfd)
         amn = float(torch.dot(zb_min, direction))
         acp = float(torch.dot(zb_comp, direction))
         checks.append({"what": label, "fd_min_lapse": fmin, "adj_min_lapse": amn, "fd_compaction": fcomp,
                        "adj_compaction": acp})
+        return t1
 
-    fd(shape, "mu")
-    rng = np.random.default_rng(2606)
-    centre = n // 2
-    for _ in range(8):
-        i, j, k = (int(v) for v in rng.integers(centre - n // 8, centre + n // 8, size=3))
-        e = torch.zeros_like(shape)
-        e[(k * n + j) * n + i] = 1.0
-        fd(e, f"zeta[{i},{j},{k}]")
-    for r in range(2):
-        d = torch.from_numpy(rng.standard_normal(n ** 3)).cuda() * shape
-        fd(d, f"random direction {r}")
+    t_fwd_plain = fd(shape, "mu")
+    if point_checks:
+        rng = np.random.default_rng(2606)
+        centre = n // 2
+        for _ in range(8):
+            i, j, k = (int(v) for v in rng.integers(centre - n // 8, centre + n // 8, size=3))
+            e = torch.zeros_like(shape)
+            e[(k * n + j) * n + i] = 1.0
+            fd(e, f"zeta[{i},{j},{k}]")
+        for r in range(2):
+            d = torch.from_numpy(rng.standard_normal(n ** 3)).cuda() * shape
+            fd(d, f"random direction {r}")
 
     def rel(a, b):
         return abs(a - b) / max(abs(a), abs(b), 1e-300)
 
-    worst_min = max(rel(c["fd_min_lapse"], c["adj_min_lapse"]) for c in checks)
-    worst_comp = max(rel(c["fd_compaction"], c["adj_compaction"]) for c in checks)
+    mu_check = checks[0]
     t_adj = t_fwd + t_bmin + t_bcomp
     nscal = n ** 3
+    res = {"grid": n, "steps": steps, "checkpoint_every": every, "mu": mu0, "sigma": 0.125, "H0L": 40.0,
+           "forward_s": t_fwd, "forward_plain_s": t_fwd_plain, "backward_min_lapse_s": t_bmin,
+           "backward_compaction_s": t_bcomp, "adjoint_total_s": t_adj,
+           "speedup_all_zeta_points": (2 * nscal * t_fwd_plain) / t_adj,
+           "speedup_11_scalars": (2 * 11 * t_fwd_plain) / t_adj,
+           "speedup_note": "finite-difference loop time (2 plain forward runs per scalar, the forward run timed "
+                           "here) / adjoint time (forward with checkpoints + one reverse per diagnostic)",
+           "min_central_lapse": float(out[0]), "min_lapse_step": rec["nstar"], "peak_compaction": float(out[1]),
+           "peak_shell": rec["kstar"], "dmin_dmu": float(g_mu_min), "dcomp_dmu": g_mu_comp,
+           "mu_fd_rel_diff_min_lapse": rel(mu_check["fd_min_lapse"], float(g_mu_min)),
+           "mu_fd_rel_diff_compaction": rel(mu_check["fd_compaction"], g_mu_comp),
+           "gpu_launches_per_forward_step": 16 + 8 + 1}  # 4 stages x 6 kernels + the central-lapse read
+    if point_checks:
+        res["fd_checks"] = checks
+        res["worst_rel_diff_min_lapse"] = max(rel(c["fd_min_lapse"], c["adj_min_lapse"]) for c in checks)
+        res["worst_rel_diff_compaction"] = max(rel(c["fd_compaction"], c["adj_compaction"]) for c in checks)
+    del run
+    torch.cuda.empty_cache()
+    return res
+
+
+def adjoint_workload(args):
+    """Gradients of collapse diagnostics at 96^3 x 256 steps as their own line, with the
+    per-point finite-difference checks."""
+    from paper_2606_02053_gb300 import build
+
+    build.build()
+    r = measure_adjoint(args.adjoint_grid, args.adjoint_steps)
+    n, steps = r["grid"], r["steps"]
     line = {"metric": f"adjoint gradient of collapse diagnostics ({n}^3, {steps} steps): speedup over finite differences",
-            "value": (2 * nscal * t_fwd) / t_adj, "unit": "x (FD loop time / adjoint time, all zeta points)",
+            "value": r["speedup_all_zeta_points"], "unit": "x (FD loop time / adjoint time, all zeta points)",
             "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "flrw_zeta_adjoint", "grid": n, "mu": mu0, "sigma": 0.125, "H0L": 40.0,
-                       "checkpoint_every": 16},
-            "forward_s": t_fwd, "backward_min_lapse_s": t_bmin, "backward_compaction_s": t_bcomp,
-            "min_central_lapse": float(out[0]), "min_lapse_step": rec["nstar"], "peak_compaction": float(out[1]),
-            "peak_shell": rec["kstar"], "dmin_dmu": g_mu_min_v, "dcomp_dmu": g_mu_comp,
-            "speedup_11_scalars": (2 * 11 * t_fwd) / t_adj, "fd_checks": checks,
-            "worst_rel_diff_min_lapse": worst_min, "worst_rel_diff_compaction": worst_comp}
+            "config": {"workload": "flrw_zeta_adjoint", "grid": n, "mu": r["mu"], "sigma": r["sigma"],
+                       "H0L": r["H0L"], "checkpoint_every": r["checkpoint_every"]}, **r}
     print(json.dumps(line), flush=True)
 
 
@@ -683,6 +746,7 @@ def main():
     g = C.make_grid(n, h)
     ev = Evolution(g, p, device=f"cuda:{local}")
     ev.init(C.make_id(0, A=0.01))
+    host_gauge_wave = ev.get() if rank == 0 and not args.no_cpu_baseline else None
     U1 = torch.empty_like(ev.state)
     U2 = torch.empty_like(ev.state)
     acc = torch.empty_like(ev.state)
@@ -766,6 +830,42 @@ def main():
     scratch = torch.empty(152 * 8 * 256, dtype=torch.float64, device=f"cuda:{local}")
     fp64_peak = max(C.cosmos_probe_fp64(scratch, stream) for _ in range(3))
 
+    # ---- the rest of the metric, on one GPU only (at N > 1 every rank would hold its GPU) ----
+    generic = batched = adjoint = None
+    if ws_ == 1 and not args.no_extras:
+        # the same sweep on a generic state: all 24 fields vary in x, y and z (the gauge wave
+        # depends on x alone, so most of its derivatives are exactly zero)
+        from paper_2606_02053_gb300 import inputs
+
+        ev.set_state(inputs.smooth_state(n, seed=2562, kmax=6, scale=0.5))
+        for w in range(3):
+            stage_calls(w * dt)
+        gk = 5
+        gev = [[[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+                for _ in range(4)] for _ in range(gk)]
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for k in range(gk):
+            stage_calls((3 + k) * dt, gev[k])
+        g1.record(stream)
+        torch.cuda.synchronize()
+        tg = g0.elapsed_time(g1) * 1e-3
+        gpass = [statistics.mean([gev[k][st][q][0].elapsed_time(gev[k][st][q][1]) for k in range(gk) for st in range(4)])
+                 for q in range(2)]
+        generic = {"value": pts * gk / tg, "unit": UNIT, "ms_per_step": 1e3 * tg / gk, "steps": gk, "warmup": 3,
+                   "derivative_pass_ms": gpass[0], "algebra_pass_ms": gpass[1],
+                   "state": "inputs.smooth_state(256, seed=2562, kmax=6, scale=0.5): every field a base value plus "
+                            "3 seeded Fourier modes with wave numbers up to 6 per axis"}
+        del ev, U1, U2, acc, dev, host_in, host_out
+        torch.cuda.empty_cache()
+        # batched threshold scan (64 instances, 64^3..96^3, fluid) against the per-instance loop;
+        # 10 of the workload's 150 steps are timed, so that the whole line stays within minutes
+        batched = measure_scan(64, 10, 3)
+        batched["steps_note"] = "10 timed steps of the 150-step workload (plus 3 warm-up); same per-step work"
+        # adjoint gradients of the collapse diagnostics, 96^3 x 256 steps, checkpoints every 16
+        adjoint = measure_adjoint(96, 256, 16, point_checks=False)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -773,8 +873,8 @@ def main():
     # ---- CPU baseline (oracle) + algorithmic flop count ----
     cpu = None
     if not args.no_cpu_baseline:
-        host_state = ev.get()
-        cpu = cpu_baseline_sample(n, planes=n, repeats=1, state=host_state)
+        host_state = host_gauge_wave
+        cpu = cpu_baseline_sample(n, planes=n // 2, repeats=1, state=host_state)
     # average launch duration per kernel (over the 4 stages and all steps)
     avg = {name: statistics.mean([x for st in pass_ms[q] for x in st]) * 1e-3
            for q, name in enumerate(["derivative", "algebra"])}
@@ -829,18 +929,19 @@ def main():
         dom = max(avg, key=avg.get)
         other = "algebra" if dom == "derivative" else "derivative"
         roof, roof2 = rf[dom](), rf[other]()
-        # the whole sweep against the slower of the FP64 rate and HBM at peak, on the algorithmic work of
-        # both passes; the stencils count as the FP64 flops they stand for although integer units do them
-        f_pt = alg_flops + oracle_flops["derivative"]
-        b_pt = bytes_point["derivative"] + bytes_point["algebra"]
-        t_f = 4 * pts * f_pt / (peak * 1e12)
-        t_b = 4 * pts * b_pt / (hbm_peak * 1e9)
-        sweep = {"bound": "alu" if t_f >= t_b else "hbm", "flops_per_point_stage": f_pt,
-                 "bytes_per_point_stage": b_pt, "roofline_ms_per_step": 1e3 * max(t_f, t_b),
-                 "fp64_ms_per_step": 1e3 * t_f, "hbm_ms_per_step": 1e3 * t_b,
-                 "ms_per_step": 1e3 * elapsed / args.steps,
-                 "frac": max(t_f, t_b) / (elapsed / args.steps),
-                 "note": "roofline time / measured time for a whole RK4 step (both passes, all 4 stages)"}
+        # the whole step against the sum of its passes' own roofline times: the algebra pass's
+        # generated FP64 operations at the FP64 peak, the derivative pass's bytes at the HBM peak
+        # (its stencils run in integer units, so no FP64 bound applies to it)
+        t_alg = 4 * pts * alg_flops / (peak * 1e12)
+        t_der = 4 * pts * bytes_point["derivative"] / (hbm_peak * 1e9)
+        t_fp64_equiv = 4 * pts * (alg_flops + oracle_flops["derivative"]) / (peak * 1e12)
+        sweep = {"roofline_ms_per_step": 1e3 * (t_alg + t_der), "algebra_fp64_ms_per_step": 1e3 * t_alg,
+                 "derivative_hbm_ms_per_step": 1e3 * t_der, "ms_per_step": 1e3 * elapsed / args.steps,
+                 "frac": (t_alg + t_der) / (elapsed / args.steps),
+                 "note": "sum of the two passes' roofline times / measured RK4 step (4 stages)",
+                 "context_fp64_equivalent_ms_per_step": 1e3 * t_fp64_equiv,
+                 "context_note": "FP64 time of the algebra plus the stencils counted as the FP64 flops they stand "
+                                 "for (integer units do them): not a bound on the executed work"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -849,6 +950,7 @@ def main():
                        "l2": "inputs larger than L2 (3.2 GB state per level)"},
             "stage_ms": stage_avg, "roofline": roof, "roofline_other_kernel": roof2, "roofline_sweep": sweep,
             "gpu_launches": gpu_launches,
+            "sweep_generic": generic, "batched": batched, "adjoint": adjoint,
             "e2e": e2e, "clocks": clk,
             "cpu_baseline": None if cpu is None else {"value": cpu["value"], "unit": UNIT, "cores": cpu["cores"],
                                                       "kind": "oracle", "sample": cpu["sample"],

@@ -440,10 +440,6 @@ int cosmos_fmr_restrict(const cosmos_fmr* m, const cosmos_params* p, int level, 
 int cosmos_constraints_noalloc(const cosmos_grid* g, const cosmos_params* p, const double* state, double* ham_mom,
                                double norms_host[8], void* stream);
 
-/* Measured FP64 fused-multiply-add throughput of the current device, in
- * flop/s (2 flop per DFMA), from a timed launch of independent DFMA chains
- * on every SM.  Synchronous; allocates nothing (writes one double per thread
- * into `scratch`, which must hold 152 * 8 * 256 doubles). */
 /* Failure detection: counts, per field, the values of `state` that are NaN
  * or Inf and, with the fluid on, the points where tau~ <= 0 (no fluid state
  * has a non-positive energy density, so the primitive recovery has no
@@ -455,12 +451,15 @@ int cosmos_constraints_noalloc(const cosmos_grid* g, const cosmos_params* p, con
 int cosmos_scan_state(const cosmos_grid* g, const cosmos_params* p, const double* state, int* counts_host, void* ws,
                       size_t ws_bytes, void* stream);
 
+/* Measured FP64 fused-multiply-add throughput of the current device, in
+ * flop/s (2 flop per DFMA), from a timed launch of independent DFMA chains
+ * on every SM.  Synchronous; allocates nothing (writes one double per thread
+ * into `scratch`, which must hold 152 * 8 * 256 doubles). */
 int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream);
 
 /* cudaError_t of the last COSMOS_ECUDA returned by this thread. */
 int cosmos_last_cuda_error(void);
 
-/* Static description of an error code. */
 /* ------------------------------------------------------------------------
  * Checkpoint / resume of one grid's state.  File: a 4096-byte text header
  * (one JSON object, padded with spaces, ending in a newline: "format"
@@ -487,6 +486,7 @@ int cosmos_checkpoint_save(const char* path, const cosmos_grid* g, const cosmos_
 int cosmos_checkpoint_load(const char* path, const cosmos_grid* g, const cosmos_params* p, double* state,
                            int state_on_device, double* t_out, long long* step_out, void* stream);
 
+/* Static description of an error code. */
 const char* cosmos_strerror(int code);
 
 #ifdef __cplusplus

@@ -56,7 +56,7 @@ static int nslot_of(const cosmos_params* p) { return 24 + 2 * p->scalar; }
 
 // BX x DBY (32 x 8) tiles of every plane: the derivative pass's work list
 static long deriv_tiles(const cosmos_grid& g) {
-  return (long)((g.nx + BX - 1) / BX) * ((g.ny + DBY - 1) / DBY) * ((g.nz + DBZ - 1) / DBZ);
+  return (long)((g.nx + BX - 1) / BX) * ((g.ny + DBY - 1) / DBY) * g.nz;
 }
 
 static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_params* p, int max_steps) {
@@ -106,7 +106,7 @@ struct cosmos_batch_s {
   long ntiles = 0, ndtiles = 0;
   StageArgs* d_args = nullptr;  // [4][n]
   BatchTile* d_tiles = nullptr;
-  BatchTile* d_dtiles = nullptr;  // derivative-pass tiles (BX x DBY x DBZ; c = plane group)
+  BatchTile* d_dtiles = nullptr;  // derivative-pass tiles (BX x DBY of one z-plane; c = the plane)
   double* d_kref = nullptr;     // [max_steps][4][n]
   cudaGraphExec_t gexec = nullptr;
   int g_first = -1, g_steps = -1;

@@ -17,10 +17,6 @@ constexpr int BY = 4;   // rows per block
 #define COSMOS_DERIV_ROWS 8
 #endif
 constexpr int DBY = COSMOS_DERIV_ROWS;  // rows per block of the derivative pass
-#ifndef COSMOS_DERIV_PLANES
-#define COSMOS_DERIV_PLANES 1
-#endif
-constexpr int DBZ = COSMOS_DERIV_PLANES;  // z-planes per block of the derivative pass
 
 // Grid description as the kernels see it.
 struct DevGrid {
@@ -176,9 +172,6 @@ cudaError_t launch_fluid_flux(const DevGrid& g, const double* U, const double* p
                               int nf_offset_fluid, cudaStream_t s);
 
 inline dim3 point_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz); }
-inline dim3 deriv_grid(const DevGrid& g) {
-  return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, (g.nz + DBZ - 1) / DBZ);
-}
 // integer derivative pass: one BX x DBY tile of one z-plane per block
 inline dim3 ideriv_grid(const DevGrid& g) { return dim3((g.nx + BX - 1) / BX, (g.ny + DBY - 1) / DBY, g.nz); }
 // Every index the integer derivative pass forms for a tile lies in [-n, 2n)

@@ -282,8 +282,8 @@ __device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, cons
       from_limbs(l_sub(l_mul(l_sub(rz[TXH], rz[-TXH]), 8), l_sub(rz[2 * TXH], rz[-2 * TXH])), e) * c.mix[2];
 }
 
-// One BX x DBY tile of one z-plane (block of BX x DBY threads), as deriv_tile
-// with the staging of one second-derivative field at a time.
+// One BX x DBY tile of one z-plane (block of BX x DBY threads); the D_y / D_z
+// sums of one second-derivative field at a time are staged in shared memory.
 template <class T, bool NEAR>
 __device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, int k, int3* __restrict__ sDy,
                                             int3* __restrict__ sDz) {

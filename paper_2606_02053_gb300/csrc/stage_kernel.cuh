@@ -5,9 +5,8 @@
 //    6th-derivative Kreiss-Oliger term of every non-fluid field, written to
 //    the derivative buffer D.  The launchers run it in exact integer
 //    arithmetic on a fixed-point copy of the state (stage_int.cuh:
-//    ideriv_kernel, batch_ideriv_kernel) whenever the arguments carry that
-//    copy, which every path of the library does; deriv_kernel and
-//    batch_deriv_kernel below are the same stencils in FP64;
+//    ideriv_kernel, batch_ideriv_kernel); the launchers refuse arguments
+//    without that copy;
 //  * algebra pass (stage_kernel, batch_stage_kernel): one point per thread,
 //    the generated pointwise BSSN + matter algebra on the state and D, the KO
 //    term or the Kurganov-Tadmor flux divergence, and the RK4 stage combine.
@@ -19,12 +18,6 @@
 
 #include "common.cuh"
 
-#ifndef COSMOS_DERIV_MIN_BLOCKS
-#define COSMOS_DERIV_MIN_BLOCKS 3  // derivative pass: resident blocks (of BX x DBY threads) per SM
-#endif
-#ifndef COSMOS_DERIV_STAGE_ALL
-#define COSMOS_DERIV_STAGE_ALL 0  // derivative pass: stage every second-derivative field behind one barrier
-#endif
 #ifndef COSMOS_STAGE_MIN_BLOCKS
 #define COSMOS_STAGE_MIN_BLOCKS 3  // resident 128-thread blocks per SM the register budget is sized for
 #endif
@@ -152,7 +145,7 @@ __device__ __forceinline__ void gather(const double* __restrict__ U, const doubl
 // ---------------------------------------------------------------------------
 // Stage = derivative pass + algebra pass.
 //
-// Derivative pass (one BX x DBY tile of DBZ z-planes per block): writes every
+// Derivative pass (one BX x DBY tile of one z-plane per block): writes every
 // finite difference the algebra needs, and the Kreiss-Oliger term of every
 // non-fluid field, into D (layout: D[3 m + d] first derivative d of the m-th
 // first-derivative field, D[3 ND1 + 6 m + p] second derivative p of the m-th
@@ -178,166 +171,6 @@ __device__ __forceinline__ long plane_off(const DevGrid& g, int x, int y, int k)
   return ((long)wrap_index(k, g.nz) * g.ny + wrap_index(y, g.ny)) * g.pitch + wrap_index(x, g.nx);
 }
 
-// Shared-memory staging of the derivative pass: the y and z first derivatives
-// of the second-derivative fields on the tile plus halo, for one field at a
-// time (DERIV_STAGE_ALL = 0) or for all of them behind a single barrier (1).
-template <class T>
-struct DerivSmem {
-  static constexpr int NST = COSMOS_DERIV_STAGE_ALL ? T::ND2 : 1;
-  static constexpr int NY = TXH * DBY, NZ = TXH * (DBY + 4);  // doubles per staged field
-};
-
-// D_y (rows j0 .. j0+DBY-1) and D_z (rows j0-2 .. j0+DBY+1) of field F on the
-// x-extended tile into sDy / sDz.
-__device__ __forceinline__ void stage_dydz(const StageArgs& a, const double* __restrict__ F, int i0, int j0, int k,
-                                           int tid, double* __restrict__ sDy, double* __restrict__ sDz) {
-  const Coef& c = a.c;
-  for (int q = tid; q < TXH * DBY; q += BX * DBY) {
-    const int qx = q % TXH, qy = q / TXH;
-    const int x = i0 - 2 + qx, y = j0 + qy;
-    const double u = ldg(F, plane_off(a.g, x, y + 1, k)) - ldg(F, plane_off(a.g, x, y - 1, k));
-    const double v = ldg(F, plane_off(a.g, x, y + 2, k)) - ldg(F, plane_off(a.g, x, y - 2, k));
-    sDy[q] = u * c.d1a[1] - v * c.d1b[1];
-  }
-  for (int q = tid; q < TXH * (DBY + 4); q += BX * DBY) {
-    const int qx = q % TXH, qy = q / TXH;
-    const int x = i0 - 2 + qx, y = j0 - 2 + qy;
-    const double u = ldg(F, plane_off(a.g, x, y, k + 1)) - ldg(F, plane_off(a.g, x, y, k - 1));
-    const double v = ldg(F, plane_off(a.g, x, y, k + 2)) - ldg(F, plane_off(a.g, x, y, k - 2));
-    sDz[q] = u * c.d1a[2] - v * c.d1b[2];
-  }
-}
-
-// Everything the algebra needs from second-derivative field m2 at point n,
-// with its staged D_y / D_z.
-template <class T>
-__device__ __forceinline__ void deriv_d2_point(const StageArgs& a, int m2, const Nbr& n, int tx, int ty, bool ko_equal,
-                                               const double* __restrict__ sDy, const double* __restrict__ sDz) {
-  const long fs = a.g.fstride;
-  const Coef& c = a.c;
-  double* __restrict__ D = a.D;
-  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
-  const int f = T::d2_field(m2);
-  const double* F = a.U + (long)f * fs;
-  const double f0 = ldg(F, n.c);
-  // per axis: s_k = (f(+k) - f0) + (f(-k) - f0) for k = 1, 2 (exact neighbour
-  // differences, shared by D2 and KO) and q3 = f(+3) + f(-3)
-  double d2[3], d1x, s1[3], s2[3], q3[3];
-  {
-    const double p1 = ldg(F, disp<0>(n, 1)) - f0, m1 = ldg(F, disp<0>(n, -1)) - f0;
-    const double p2 = ldg(F, disp<0>(n, 2)) - f0, m2v = ldg(F, disp<0>(n, -2)) - f0;
-    d1x = (p1 - m1) * c.d1a[0] - (p2 - m2v) * c.d1b[0];
-    s1[0] = p1 + m1;
-    s2[0] = p2 + m2v;
-    q3[0] = ldg(F, disp<0>(n, 3)) + ldg(F, disp<0>(n, -3));
-  }
-  s1[1] = (ldg(F, disp<1>(n, 1)) - f0) + (ldg(F, disp<1>(n, -1)) - f0);
-  s2[1] = (ldg(F, disp<1>(n, 2)) - f0) + (ldg(F, disp<1>(n, -2)) - f0);
-  q3[1] = ldg(F, disp<1>(n, 3)) + ldg(F, disp<1>(n, -3));
-  s1[2] = (ldg(F, disp<2>(n, 1)) - f0) + (ldg(F, disp<2>(n, -1)) - f0);
-  s2[2] = (ldg(F, disp<2>(n, 2)) - f0) + (ldg(F, disp<2>(n, -2)) - f0);
-  q3[2] = ldg(F, disp<2>(n, 3)) + ldg(F, disp<2>(n, -3));
-#pragma unroll
-  for (int d = 0; d < 3; ++d) d2[d] = s1[d] * c.d2a[d] - s2[d] * c.d2b[d];
-  // KO bracket per axis: (q3 - 2 f0) - 6 s2 + 15 s1, exactly zero for constants
-  double ko = 0.0;
-  if (a.skip_ko) {
-  } else if (ko_equal) {
-    const double Q3 = ((q3[0] + q3[1]) + q3[2]) - __dmul_rn(6.0, f0);
-    ko = fma(15.0, (s1[0] + s1[1]) + s1[2], fma(-6.0, (s2[0] + s2[1]) + s2[2], Q3));  // scaled in the algebra pass
-  } else {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) ko = fma(c.ko[d], fma(15.0, s1[d], fma(-6.0, s2[d], q3[d] - 2.0 * f0)), ko);
-  }
-  const double* ry = sDy + ty * TXH + tx + 2;        // D_y at (i + o, j)
-  const double* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z at (i + o, j), row stride TXH along y
-  const double dxy = (ry[1] - ry[-1]) * c.d1a[0] - (ry[2] - ry[-2]) * c.d1b[0];
-  const double dxz = (rz[1] - rz[-1]) * c.d1a[0] - (rz[2] - rz[-2]) * c.d1b[0];
-  const double dyz = (rz[TXH] - rz[-TXH]) * c.d1a[1] - (rz[2 * TXH] - rz[-2 * TXH]) * c.d1b[1];
-  const int m1 = T::d1_slot(f);
-  D[(long)(3 * m1 + 0) * fs + n.c] = d1x;
-  D[(long)(3 * m1 + 1) * fs + n.c] = ry[0];
-  D[(long)(3 * m1 + 2) * fs + n.c] = rz[0];
-  const long b = (long)(3 * T::ND1 + 6 * m2) * fs + n.c;
-  D[b + 0 * fs] = d2[0];
-  D[b + 1 * fs] = dxy;
-  D[b + 2 * fs] = dxz;
-  D[b + 3 * fs] = d2[1];
-  D[b + 4 * fs] = dyz;
-  D[b + 5 * fs] = d2[2];
-  if (!a.skip_ko) D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] = ko;
-}
-
-// One BX x DBY tile of the DBZ z-planes k0 .. k0 + DBZ - 1 (block of
-// BX x DBY x DBZ threads; each plane stages into its own shared-memory slice).
-template <class T>
-__device__ __forceinline__ void deriv_tile(const StageArgs& a, int i0, int j0, int k0, double* __restrict__ sDy,
-                                           double* __restrict__ sDz) {
-  using S = DerivSmem<T>;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-  const int i = i0 + tx, j = j0 + ty, k = k0 + (int)threadIdx.z;
-  const bool plane_ok = k < a.g.nz;  // same for the whole slice
-  const bool valid = i < a.g.nx && j < a.g.ny && plane_ok;
-  sDy += threadIdx.z * (S::NST * S::NY);
-  sDz += threadIdx.z * (S::NST * S::NZ);
-  const Nbr n = make_nbr(a.g, i, j, k);
-  const long fs = a.g.fstride;
-  const Coef& c = a.c;
-  double* __restrict__ D = a.D;
-  constexpr int NDER0 = 3 * T::ND1 + 6 * T::ND2;
-  const bool ko_equal = c.ko[0] == c.ko[1] && c.ko[1] == c.ko[2];  // same for every thread
-  const int f_lo = a.f_lo, f_hi = a.f_hi > 0 ? a.f_hi : (1 << 30);  // field range (uniform)
-  if constexpr (S::NST > 1) {
-#pragma unroll 1
-    for (int m2 = 0; m2 < T::ND2; ++m2) {
-      const int f = T::d2_field(m2);
-      if (f >= f_lo && f < f_hi && plane_ok)
-        stage_dydz(a, a.U + (long)f * fs, i0, j0, k, tid, sDy + m2 * S::NY, sDz + m2 * S::NZ);
-    }
-  }
-  // fields with first derivatives only: direct D1 and KO
-#pragma unroll 1
-  for (int m = 0; m < T::ND1; ++m) {
-    const int f = T::d1_field(m);
-    if (T::d2_slot(f) >= 0 || f < f_lo || f >= f_hi) continue;
-    const double* F = a.U + (long)f * fs;
-    if (valid) {
-      D[(long)(3 * m + 0) * fs + n.c] = fd1<0>(F, n, c);
-      D[(long)(3 * m + 1) * fs + n.c] = fd1<1>(F, n, c);
-      D[(long)(3 * m + 2) * fs + n.c] = fd1<2>(F, n, c);
-      if (!a.skip_ko)
-        D[(long)(NDER0 + ko_slot<T>(f)) * fs + n.c] =
-            ko_equal ? ko_bracket(F, n, ldg(F, n.c)) : ko_add(F, n, c, ldg(F, n.c), 0.0);
-    }
-  }
-  // fields with second derivatives
-  if constexpr (S::NST > 1) {
-    __syncthreads();
-    if (valid) {
-#pragma unroll 1
-      for (int m2 = 0; m2 < T::ND2; ++m2) {
-        const int f = T::d2_field(m2);
-        if (f >= f_lo && f < f_hi) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy + m2 * S::NY, sDz + m2 * S::NZ);
-      }
-    }
-    __syncthreads();  // the staging area is reused by the block's next tile
-  } else {
-#pragma unroll 1
-    for (int m2 = 0; m2 < T::ND2; ++m2) {
-      if (T::d2_field(m2) < f_lo || T::d2_field(m2) >= f_hi) continue;  // uniform across the block
-      if (plane_ok) stage_dydz(a, a.U + (long)T::d2_field(m2) * fs, i0, j0, k, tid, sDy, sDz);
-      __syncthreads();
-      if (valid) deriv_d2_point<T>(a, m2, n, tx, ty, ko_equal, sDy, sDz);
-      __syncthreads();
-    }
-  }
-}
-
-template <class T>
-__global__ void __launch_bounds__(BX* DBY* DBZ, COSMOS_DERIV_MIN_BLOCKS) deriv_kernel(const StageArgs a) {
-  __shared__ double sDy[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NZ];
-  deriv_tile<T>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z * DBZ, sDy, sDz);
-}
 }  // namespace cosmos
 
 #include "stage_int.cuh"
@@ -446,17 +279,6 @@ __device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g
   return true;
 }
 
-// Persistent batched derivative pass over BX x DBY tiles of every instance.
-template <class T>
-__global__ void __launch_bounds__(BX* DBY* DBZ, COSMOS_DERIV_MIN_BLOCKS)
-    batch_deriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
-  __shared__ double sDy[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NY], sDz[DBZ * DerivSmem<T>::NST * DerivSmem<T>::NZ];
-  for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
-    const BatchTile t = tiles[w];
-    deriv_tile<T>(args[t.inst], t.a * BX, t.b * DBY, t.c * DBZ, sDy, sDz);
-  }
-}
-
 // Persistent batched algebra pass: blocks stride over the flat work list of
 // all instances; instance `inst` uses args[inst] with K_ref taken from kref.
 template <class T, int MODE>
@@ -550,12 +372,11 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
     dim3 grid = point_grid(a.g), block(BX, BY);                                                                \
     if (a.k_cnt > 0) grid.z = a.k_cnt;                                                                          \
     if (mode < 0 || !(mode & 8)) {                                                                            \
-      if (a.L && near_indices(a.g))                                                                            \
+      if (!a.L) return cudaErrorInvalidValue; /* the derivative pass reads the limb copy */                     \
+      if (near_indices(a.g))                                                                                    \
         ideriv_kernel<T_##NAME, true><<<ideriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);                            \
-      else if (a.L)                                                                                             \
-        ideriv_kernel<T_##NAME, false><<<ideriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);                           \
       else                                                                                                      \
-        deriv_kernel<T_##NAME><<<deriv_grid(a.g), dim3(BX, DBY, DBZ), 0, s>>>(a);                               \
+        ideriv_kernel<T_##NAME, false><<<ideriv_grid(a.g), dim3(BX, DBY), 0, s>>>(a);                           \
     }                                                                                                           \
     if (mode < 0) return cudaGetLastError();                                                                    \
     switch (mode & 7) {                                                                                             \
@@ -570,12 +391,11 @@ __global__ void __launch_bounds__(BX* BY, 2) constraint_kernel(const ConstraintA
                                         const double* kref, int mode, dim3 grid, dim3 block, cudaStream_t s,      \
                                         const BatchTile* dtiles, long ndtiles, int ideriv_blocks,                 \
                                         bool ideriv_near) {                                                       \
-    if (ideriv_blocks > 0 && ideriv_near)                                                                       \
+    if (ideriv_blocks <= 0) return cudaErrorInvalidValue;                                                       \
+    if (ideriv_near)                                                                                            \
       batch_ideriv_kernel<T_##NAME, true><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);       \
-    else if (ideriv_blocks > 0)                                                                                 \
-      batch_ideriv_kernel<T_##NAME, false><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);      \
     else                                                                                                        \
-      batch_deriv_kernel<T_##NAME><<<grid, dim3(BX, DBY, DBZ), 0, s>>>(args, dtiles, ndtiles);                  \
+      batch_ideriv_kernel<T_##NAME, false><<<ideriv_blocks, dim3(BX, DBY), 0, s>>>(args, dtiles, ndtiles);      \
     switch (mode) {                                                                                             \
       case MODE_S1:                                                                                             \
         batch_stage_kernel<T_##NAME, MODE_S1><<<grid, block, 0, s>>>(args, tiles, ntiles, mapping, kref);       \
