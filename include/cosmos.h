@@ -132,9 +132,19 @@ size_t cosmos_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int 
 int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
                      size_t ws_bytes, void* stream);
 
-/* Right-hand side d_t U = F(U, t) of every field (BSSN equations, gauge,
- * matter sources, Kreiss-Oliger dissipation, KT flux divergence), written
- * to `rhs` (same layout as state).  ws: COSMOS_OP_RHS bytes. */
+/* Right-hand side d_t U = F(U, t) of every field, written to `rhs` (same
+ * layout as state).  Section "Physical system settings": the Einstein
+ * equations G = 8 pi T with T = T^SC + T^FL (here in the BSSN chi-form the
+ * paper leaves to the textbooks it cites: conformal metric, trace-free
+ * extrinsic curvature, K, conformal connection functions, 1+log or harmonic
+ * slicing with the background trace K_ref(t), Gamma-driver shift), the
+ * matter sources rho_H, J_i, S_ij of the perfect fluid P = w rho and of the
+ * massless scalar (box phi = 0), and the fluid's conservation law
+ * div T^FL = 0 in conservative 3+1 form with Kurganov-Tadmor face fluxes
+ * (same section, last sentence of its first part).  4th-order centred
+ * differences; 6th-derivative Kreiss-Oliger dissipation on every field but
+ * the fluid's.  ws: COSMOS_OP_RHS bytes.  Errors: COSMOS_EINVAL (grid or
+ * parameters, NULL buffer), COSMOS_EALIGN, COSMOS_EWORKSPACE, COSMOS_ECUDA. */
 int cosmos_rhs(const cosmos_grid* g, const cosmos_params* p, const double* state, double* rhs, double t, void* ws,
                size_t ws_bytes, void* stream);
 
@@ -161,9 +171,12 @@ int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, in
                       double* U_n, double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes,
                       void* stream);
 
-/* One classic RK4 step of size dt from time t, in place on `state`
- * (four cosmos_rk4_stage launches).  ws: COSMOS_OP_RK4 bytes
- * (two stage buffers, the accumulator and the fluid buffers). */
+/* One classic RK4 step of size dt from time t of the evolution problem of
+ * section "Physical system settings" (the right-hand side of cosmos_rhs),
+ * in place on `state`: k_s = F(U_s, t + c_s dt), U_{n+1} = U_n + dt/6
+ * (k1 + 2 k2 + 2 k3 + k4), as four cosmos_rk4_stage calls, each fused with
+ * its stage combine.  ws: COSMOS_OP_RK4 bytes (two stage buffers, the
+ * accumulator and the fluid buffers).  Errors as cosmos_rhs. */
 int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
                     size_t ws_bytes, void* stream);
 
@@ -189,7 +202,10 @@ int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double*
 int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
                        double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
-/* Hamiltonian and (conformal) momentum constraints
+/* Hamiltonian and (conformal) momentum constraints, the parts of the
+ * Einstein equations that the initial data must satisfy (section "Physical
+ * system settings", initial-data paragraph: the fluid is generated to meet
+ * them, and they hold to rounding precision at the start)
  *   H   = R + 2/3 K^2 - At_ij At^ij - 16 pi rho_H
  *   M^i = gt^ik gt^jl Dt_j At_kl - 3/(2 chi) At^ij d_j chi - 2/3 gt^ij d_j K - 8 pi gt^ij J_j
  * per point into ham_mom (4 fields in state layout, or NULL) and their norms
@@ -218,9 +234,13 @@ size_t cosmos_adjoint_workspace_bytes(const cosmos_grid* g, const cosmos_params*
 int cosmos_rhs_vjp(const cosmos_grid* g, const cosmos_params* p, const double* U, const double* w, double* v,
                    double t, void* ws, size_t ws_bytes, void* stream);
 
-/* Adjoint of one RK4 step U_{n+1} = Phi(U_n) from time t with step dt:
- * lam_n = (dPhi/dU_n)^T lam_np1.  Recomputes the stage states from U_n.
- * lam_n may equal lam_np1 (in place). */
+/* Adjoint of one RK4 step U_{n+1} = Phi(U_n) of cosmos_rk4_step from time t
+ * with step dt: lam_n = (dPhi/dU_n)^T lam_np1, stage by stage in reverse
+ * (the paper has no adjoint: this serves gradients of the collapse
+ * diagnostics of its PBH examples, section "Examples", with respect to the
+ * initial curvature perturbation of its initial-data paragraph).
+ * Recomputes the stage states from U_n.  lam_n may equal lam_np1 (in
+ * place).  ws: COSMOS_OP_ADJOINT bytes.  Errors as cosmos_rhs. */
 int cosmos_adjoint_step(const cosmos_grid* g, const cosmos_params* p, const double* U_n, const double* lam_np1,
                         double* lam_n, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
@@ -415,12 +435,14 @@ int cosmos_fmr_restrict(const cosmos_fmr* m, const cosmos_params* p, int level, 
                         void* stream);
 
 /* cosmos_constraints without a workspace argument, for callers that cannot
- * allocate device memory: code that runs while a stream is being captured
- * into a CUDA graph, inside host callbacks, or in a host application whose
- * memory pool forbids cudaMalloc/cudaFree (and the device-wide
- * synchronisation they can imply) once it is running.  The paper has no
- * counterpart; this is a library-usage variant of cosmos_constraints with the
- * same outputs and the same synchronous behaviour.
+ * allocate device memory while they run: a host application whose device
+ * memory is handed out by its own pool or framework, which forbids
+ * cudaMalloc/cudaFree once it is running (they can synchronise the whole
+ * device and stall its other streams), or a monitoring hook that must not
+ * change the process's memory footprint.  The paper has no counterpart; this
+ * is a library-usage variant of cosmos_constraints with the same outputs and
+ * the same synchronous behaviour: it copies the norms to the host and
+ * synchronises `stream` before it returns.
  *
  * Scratch: one static device array of 2^21 doubles (16 MiB) inside the
  * library, which every GPU that loads the library keeps until the process
@@ -429,9 +451,12 @@ int cosmos_fmr_restrict(const cosmos_fmr* m, const cosmos_params* p, int level, 
  * 32) + 8 doubles; larger grids return COSMOS_EWORKSPACE before anything is
  * launched (e.g. 256^3 vacuum fits; with the fluid on, up to about 80^3).
  * The first call made with a device current resolves the array's device
- * address for that device (cudaGetSymbolAddress); make that first call
- * before any stream capture.  The call allocates nothing: no cudaMalloc,
- * cudaFree or allocating library routine.
+ * address for that device (cudaGetSymbolAddress) and keeps it for the rest
+ * of the process; make that first call before any stream capture.  After a
+ * cudaDeviceReset the kept address may no longer be valid: this call is not
+ * for processes that reset a device they have used it on.  The call
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Arguments are checked as cosmos_constraints checks them.
  * Every call overwrites all the scratch it reads, so no state carries over
  * between calls, but all calls share the one array: calls that can overlap
  * on the GPU (other streams, other host threads) race and must be
@@ -481,8 +506,11 @@ int cosmos_checkpoint_save(const char* path, const cosmos_grid* g, const cosmos_
 /* Reads `path` into `state` and returns its time and step counter.  The
  * header must give exactly this grid (sizes, spacing, origin) and these
  * parameters, and the payload must have the stated size and hash, else
- * COSMOS_ECHECKPOINT and `state` is not written.  Errors also COSMOS_EINVAL,
- * COSMOS_EIO, COSMOS_ECUDA. */
+ * COSMOS_ECHECKPOINT and `state` is not written (a first pass over the file
+ * checks all of this; a second pass copies the payload in, hashing it again).
+ * COSMOS_EIO: the file failed to read, or changed, during the second pass;
+ * `state` then holds part of the file or unverified data and must not be
+ * used.  Errors also COSMOS_EINVAL, COSMOS_ECUDA. */
 int cosmos_checkpoint_load(const char* path, const cosmos_grid* g, const cosmos_params* p, double* state,
                            int state_on_device, double* t_out, long long* step_out, void* stream);
 

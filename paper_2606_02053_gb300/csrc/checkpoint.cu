@@ -243,11 +243,15 @@ int cosmos_checkpoint_load(const char* path, const cosmos_grid* g, const cosmos_
     fclose(fp);
     return COSMOS_ECHECKPOINT;
   }
+  // the second pass is hashed too: a file rewritten or failing between the
+  // passes is reported (the state then holds unverified data: COSMOS_EIO)
+  uint64_t hash2 = kFnvOffset;
   for (int f = 0; f < nf; ++f) {
     if (fread(buf.data(), sizeof(double), npts, fp) != npts) {
       fclose(fp);
       return COSMOS_EIO;
     }
+    hash2 = fnv1a(hash2, (const unsigned char*)buf.data(), npts * sizeof(double));
     e = copy_field(g, state, state_on_device, f, buf.data(), false, (cudaStream_t)stream);
     if (e) {
       fclose(fp);
@@ -255,6 +259,7 @@ int cosmos_checkpoint_load(const char* path, const cosmos_grid* g, const cosmos_
     }
   }
   fclose(fp);
+  if (hash2 != hash) return COSMOS_EIO;
   if (t_out) *t_out = t;
   if (step_out) *step_out = (long long)stp;
   return COSMOS_OK;

@@ -74,13 +74,10 @@ using namespace cosmos;
 
 extern "C" int cosmos_constraints_noalloc(const cosmos_grid* g, const cosmos_params* p, const double* state,
                                           double* ham_mom, double norms_host[8], void* stream) {
-  if (!g || !p || !state || !norms_host) return COSMOS_EINVAL;
-  if (g->nx < 1 || g->ny < 1 || g->nz < 1 || g->pitch < g->nx || g->nz > 65535 || (g->ny + BY - 1) / BY > 65535)
-    return COSMOS_EINVAL;
-  for (int d = 0; d < 3; ++d)
-    if (!(g->h[d] > 0.0)) return COSMOS_EINVAL;
-  if ((p->fluid != 0 && p->fluid != 1) || (p->scalar != 0 && p->scalar != 1)) return COSMOS_EINVAL;
-  if (p->fluid && !(p->w > 0.0 && p->w <= 1.0)) return COSMOS_EINVAL;
+  // the same argument checks as cosmos_constraints, then the scratch size
+  const int v = validate(g, p);
+  if (v != COSMOS_OK) return v;
+  if (!state || !norms_host) return COSMOS_EINVAL;
   if (((uintptr_t)state & 15u) || ((uintptr_t)ham_mom & 15u)) return COSMOS_EALIGN;
 
   const DevGrid dg = make_devgrid(g);

@@ -91,6 +91,25 @@ def test_host_side_validation_without_gpu(libpath):
     assert C.lib().cosmos_rhs(ctypes.byref(g), ctypes.byref(pw), None, None, 0.0, None, 0, None) == C.COSMOS_EINVAL
 
 
+def test_both_constraint_entry_points_check_arguments_alike(libpath):
+    """cosmos_constraints and its static-scratch variant refuse the same grids and
+    parameters before any launch: here a small grid whose row pitch makes one field
+    2^31 elements or more, a non-finite spacing and a negative KO strength."""
+    from paper_2606_02053_gb300 import cosmos as C
+
+    norms = (ctypes.c_double * 8)()
+    fake_state = ctypes.c_void_p(1 << 12)  # never dereferenced: refused first
+    p = C.make_params()
+    cases = [(C.make_grid((32, 16, 16), 0.05, pitch=1 << 23), p),
+             (C.make_grid((32, 16, 16), float("inf")), p),
+             (C.make_grid((32, 16, 16), 0.05), C.make_params(ko_sigma=-0.1))]
+    for g, pp in cases:
+        assert C.lib().cosmos_constraints(ctypes.byref(g), ctypes.byref(pp), fake_state, None, norms, None, 0,
+                                          None) == C.COSMOS_EINVAL
+        assert C.lib().cosmos_constraints_noalloc(ctypes.byref(g), ctypes.byref(pp), fake_state, None, norms,
+                                                  None) == C.COSMOS_EINVAL
+
+
 def test_state_scan_host_checks_without_gpu(libpath):
     """The failure-detection scan sizes its workspace (one count per field) and
     refuses bad arguments before touching the device."""

@@ -1,12 +1,12 @@
 """cosmos_constraints_noalloc against cosmos_constraints, through the C ABI.
 
-The no-allocation variant is for callers that cannot call cudaMalloc (code
-running under stream capture, in host callbacks, or in applications whose
-memory pool forbids device allocation): its scratch is a static device array
-inside the library.  It must give the same constraint fields and norms as
-the workspace-taking entry point, on repeated calls (the shared array keeps
-the previous call's contents, which must not leak into the next result), and
-reject grids that do not fit the array before launching anything.
+The no-allocation variant is for callers that cannot call cudaMalloc while
+they run (applications whose device memory is handed out by their own pool
+or framework): its scratch is a static device array inside the library.  It
+must give the same constraint fields and norms as the workspace-taking entry
+point, on repeated calls (the shared array keeps the previous call's
+contents, which must not leak into the next result), and reject grids that
+do not fit the array before launching anything.
 This file is collected last on purpose.
 """
 import ctypes
