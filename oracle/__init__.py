@@ -15,7 +15,11 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
       cross-check against an autodiff evaluation of the Einstein equations
       (vacuum, fluid, scalar), homogeneous FLRW expansion law.
   constraints : autodiff ADM constraints (4th-order convergence), gauge wave.
-  init        : gauge-wave closed form; FLRW + zeta gives H = 0 (discrete).
+  init        : gauge-wave closed form; FLRW + zeta gives H = 0 (discrete);
+      next-to-leading-order data (kind 3): the right-hand side at t = 0 meets
+      the growing-mode rates of K, At and gt to O(eps^4) (16-fold per doubling
+      of H0; 4-fold for the leading-order data or a wrong coefficient), H = 0,
+      M = 0, and the data reduce to the leading order as eps -> 0.
   flop_count  : counts only; no physics.
   fluid_rho   : round trip (rho, v) -> (E, J) -> rho against the definitions.
   rhs_vjp / adjoint_step : tape reverse mode of rhs / rk4_step; pinned by

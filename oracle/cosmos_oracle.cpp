@@ -1021,11 +1021,21 @@ void rk4_step(const Grid& g, const Params& P, double* state, double t, double dt
 /*          the fluid E takes the rest of the discrete Hamiltonian          */
 /*          constraint: E = (R + 2/3 K^2 - At.At)/(16 pi) - rho_phi with    */
 /*          rho_phi = 1/2 chi gt^ij d_i phi d_j phi (fluid and scalar on).  */
+/*  kind 3: kind 1 carried to the next-to-leading order of the gradient     */
+/*          expansion (section "Physical system settings", initial-data     */
+/*          paragraph: growing mode up to next-leading order in k/(aH));   */
+/*          the formulas are derived here, see init_nlo.                    */
 /* id[] = {kind, A, mu, sigma, q0, q1, q2, c0, c1, c2, a0, t}               */
 /* ------------------------------------------------------------------------ */
 /* Lx: wavelength of the gauge wave (0: the grid's own length n_x h_x). */
+void init_nlo(const Grid& g, const Params& P, const double* id, double* state);
+
 void init_all(const Grid& g, const Params& P, const double* id, double* state, double Lx_wave = 0.0) {
   const int kind = (int)id[0];
+  if (kind == 3) {
+    init_nlo(g, P, id, state);
+    return;
+  }
   const long N = g.npts();
   const int nf = P.nf();
   std::fill(state, state + (long)nf * N, 0.0);
@@ -1104,6 +1114,123 @@ void init_all(const Grid& g, const Params& P, const double* id, double* state, d
       state[q * N + m] = E[m] / (chi * std::sqrt(chi));
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Next-to-leading-order long-wavelength data (kind 3).  The paper takes     */
+/* the growing mode of the gradient expansion in eps = k/(aH) up to the next */
+/* order and leaves the formulas to the papers it cites; they are derived    */
+/* here.  Background: flat FLRW filled with P = w rho, a ~ t^{2/(3(1+w))},  */
+/* slices of constant mean curvature K = -3 H(t), zero shift.  Leading       */
+/* order: gamma_ij = a^2 psi^4 delta_ij with psi = e^{zeta/2} fixed in time */
+/* (chi0 = a^-2 psi^-4), K_ij = -H gamma_ij, alpha = 1.  Every O(eps^2)      */
+/* correction of the growing mode is proportional to g(t) = 1/(a H)^2, whose */
+/* rate is d ln g/dt = (1 + 3w) H.  With R_ij the Ricci tensor of the        */
+/* leading-order metric (lower indices, the same for any constant scale),    */
+/* M_ij = R_ij - 1/3 delta_ij delta^kl R_kl and R = chi0 delta^kl R_kl:      */
+/*  - trace-free evolution d_t At_ij = chi R_ij^TF - 3 H At_ij + O(eps^4)    */
+/*    (D_i D_j alpha and S_ij^TF are O(eps^4)); its growing solution         */
+/*    At_ij = 2 chi0 M_ij / ((5 + 3w) H);                                   */
+/*  - d_t gt_ij = -2 At_ij: gt_ij = delta_ij + h_ij,                         */
+/*    h_ij = -4 chi0 M_ij / ((5 + 3w)(1 + 3w) H^2), taken to unit            */
+/*    determinant (which changes it at O(eps^4));                           */
+/*  - Hamiltonian constraint: delta = (E - E_b)/E_b = R / (6 H^2);           */
+/*  - d_t K = 0 (constant mean curvature) with the K equation fixes the      */
+/*    lapse: alpha = 1 - (1 + 3w) delta / (3 (1 + w));                      */
+/*  - d_t ln chi = -2 alpha H puts that lapse into the conformal factor:     */
+/*    chi = chi0 (1 + 2 delta / (3 (1 + w)));                                */
+/*  - beta = B = 0; Gt^i = gt^jk Gt^i_jk of the new gt (4th-order            */
+/*    differences, so the conformal-connection constraint holds to           */
+/*    rounding); E and J_i from the discrete Hamiltonian and momentum        */
+/*    constraints of the new metric (J = O(eps^3): the fluid is no longer   */
+/*    at rest), as the paper's data meet the constraints to rounding.       */
+/* R_ij and R are those of the right-hand side (geometry()) on the          */
+/* leading-order data; H = H0 and a = a0 at the initial time.  Needs the     */
+/* fluid on and H0 > 0.                                                      */
+/* ------------------------------------------------------------------------ */
+void init_nlo(const Grid& g, const Params& P, const double* id, double* state) {
+  const long N = g.npts();
+  const int nf = P.nf();
+  const double w = P.w, H0 = P.H0;
+  std::fill(state, state + (long)nf * N, 0.0);
+  // leading-order metric (kind 1 without its fluid)
+  Params Pv = P;
+  Pv.fluid = 0;
+  Pv.scalar = 0;
+  std::vector<double> lo((size_t)NBSSN * N);
+  std::vector<double> id1(id, id + 12);
+  id1[0] = 1.0;
+  init_all(g, Pv, id1.data(), lo.data());
+  // O(eps^2) corrections from the leading-order Ricci tensor
+  std::vector<double> nlo(lo);
+  Field F0{&g, lo.data()};
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        const long m = (k * g.n[1] + j) * g.n[0] + i;
+        Pt p{{i, j, k}};
+        Local<double> L;
+        gather<double>(F0, Pv, p, L);
+        Geom<double> G;
+        geometry<double>(L, G);
+        const double chi0 = L.chi;
+        const double trR = G.Ric[0][0] + G.Ric[1][1] + G.Ric[2][2];
+        const double delta = G.Rs / (6.0 * H0 * H0);
+        double M[3][3], gm[3][3];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            M[a][b] = G.Ric[a][b] - (a == b ? trR / 3.0 : 0.0);
+            const double h = -4.0 * chi0 * M[a][b] / ((5.0 + 3.0 * w) * (1.0 + 3.0 * w) * H0 * H0);
+            gm[a][b] = (a == b ? 1.0 : 0.0) + h;
+          }
+        const double det = gm[0][0] * (gm[1][1] * gm[2][2] - gm[1][2] * gm[2][1]) -
+                           gm[0][1] * (gm[1][0] * gm[2][2] - gm[1][2] * gm[2][0]) +
+                           gm[0][2] * (gm[1][0] * gm[2][1] - gm[1][1] * gm[2][0]);
+        const double s = 1.0 / std::cbrt(det);
+        for (int a = 0; a < 3; ++a)
+          for (int b = a; b < 3; ++b) {
+            nlo[(GT + sym(a, b)) * N + m] = gm[a][b] * s;
+            nlo[(AT + sym(a, b)) * N + m] = 2.0 * chi0 * M[a][b] / ((5.0 + 3.0 * w) * H0);
+          }
+        nlo[CHI * N + m] = chi0 * (1.0 + 2.0 * delta / (3.0 * (1.0 + w)));
+        nlo[ALP * N + m] = 1.0 - (1.0 + 3.0 * w) * delta / (3.0 * (1.0 + w));
+      }
+  // conformal connection functions of the new conformal metric
+  std::vector<double> gam(3 * (size_t)N);
+  Field F1{&g, nlo.data()};
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        Pt p{{i, j, k}};
+        Local<double> L;
+        gather<double>(F1, Pv, p, L);
+        Geom<double> G;
+        geometry<double>(L, G);
+        for (int a = 0; a < 3; ++a) gam[a * N + (k * g.n[1] + j) * g.n[0] + i] = G.Gd[a];
+      }
+  for (int a = 0; a < 3; ++a)
+    for (long m = 0; m < N; ++m) nlo[(GAM + a) * N + m] = gam[a * N + m];
+  // fluid E and J_i from the discrete constraints of the final metric (no matter in Pv)
+  for (int f = 0; f < NBSSN; ++f)
+    for (long m = 0; m < N; ++m) state[f * N + m] = nlo[f * N + m];
+  Field F2{&g, nlo.data()};
+  const int q = P.ifl();
+  for (long k = 0; k < g.n[2]; ++k)
+    for (long j = 0; j < g.n[1]; ++j)
+      for (long i = 0; i < g.n[0]; ++i) {
+        const long m = (k * g.n[1] + j) * g.n[0] + i;
+        Pt p{{i, j, k}};
+        double c[4];
+        point_constraints(F2, Pv, p, c);  // H = 16 pi E, M^i = 8 pi gt^ij J_j when they vanish
+        const double chi = nlo[CHI * N + m];
+        const double chi32 = chi * std::sqrt(chi);
+        state[q * N + m] = c[0] / (16.0 * PI) / chi32;
+        for (int a = 0; a < 3; ++a) {
+          double Ja = 0.0;
+          for (int b = 0; b < 3; ++b) Ja = Ja + nlo[(GT + sym(a, b)) * N + m] * c[1 + b];
+          state[(q + 1 + a) * N + m] = Ja / (8.0 * PI) / chi32;
+        }
+      }
 }
 
 /* ------------------------------------------------------------------------ */
