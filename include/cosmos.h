@@ -107,7 +107,23 @@ typedef struct {
                         (2 sigma^2)), Pi = 0, and E = (R + 2/3 K^2 -
                         At.At)/(16 pi) - 1/2 chi gt^ij d_i phi d_j phi, so the
                         discrete Hamiltonian constraint with both sources
-                        vanishes (requires fluid and scalar on) */
+                        vanishes (requires fluid and scalar on);
+                     3: kind 1 at the next-to-leading order of the gradient
+                        expansion in eps = k/(aH) (section "Physical system
+                        settings", initial-data paragraph: the growing mode
+                        up to the next-leading order), constant-mean-
+                        curvature slicing, zero shift: with R_ij the Ricci
+                        tensor of the leading-order metric (chi0 = a0^-2
+                        e^{-2 zeta}, gt = delta), M_ij its trace-free part,
+                        delta = chi0 tr R / (6 H0^2):
+                        At_ij = 2 chi0 M_ij / ((5 + 3w) H0),
+                        gt_ij = delta_ij + h_ij at unit determinant,
+                        h_ij = -4 chi0 M_ij / ((5 + 3w)(1 + 3w) H0^2),
+                        alpha = 1 - (1 + 3w) delta / (3 (1 + w)),
+                        chi = chi0 (1 + 2 delta / (3 (1 + w))), K = -3 H0,
+                        Gt^i = gt^jk Gt^i_jk, and the fluid's E and J_i from
+                        the discrete Hamiltonian and momentum constraints
+                        (requires fluid on and H0 > 0; scalar, if on, zero) */
   double A;
   double mu, sigma;
   double q[3];
@@ -128,7 +144,8 @@ size_t cosmos_workspace_bytes(const cosmos_grid* g, const cosmos_params* p, int 
 /* Initial data (section "Physical system settings", initial-data paragraph).
  * Writes every field of `state`.  ws: COSMOS_OP_INIT bytes.  Errors:
  * COSMOS_EINVAL (unknown kind, gauge wave with fluid, kind 2 without fluid
- * and scalar, sigma, a0 or q not positive), COSMOS_EALIGN, COSMOS_EWORKSPACE. */
+ * and scalar, kind 3 without fluid or with H0 <= 0, sigma, a0 or q not
+ * positive), COSMOS_EALIGN, COSMOS_EWORKSPACE. */
 int cosmos_init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
                      size_t ws_bytes, void* stream);
 

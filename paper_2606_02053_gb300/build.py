@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcosmos_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
-SOURCES = ["api.cu", "noalloc.cu", "checkpoint.cu", "batch.cu", "fmr.cu", "limbs.cu", "adjoint.cu", "adjoint_vac.cu", "adjoint_fluid.cu", "adjoint_scalar.cu", "adjoint_fluid_scalar.cu", "fluid.cu", "stage_vac.cu", "stage_fluid.cu", "stage_scalar.cu", "stage_fluid_scalar.cu"]
+SOURCES = ["api.cu", "init_nlo.cu", "noalloc.cu", "checkpoint.cu", "batch.cu", "fmr.cu", "limbs.cu", "adjoint.cu", "adjoint_vac.cu", "adjoint_fluid.cu", "adjoint_scalar.cu", "adjoint_fluid_scalar.cu", "fluid.cu", "stage_vac.cu", "stage_fluid.cu", "stage_scalar.cu", "stage_fluid_scalar.cu"]
 
 
 def nvcc() -> str:

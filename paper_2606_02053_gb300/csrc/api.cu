@@ -386,9 +386,10 @@ int init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id,
   if (e) return e;
   if (!id || !state) return COSMOS_EINVAL;
   if (!aligned16(state)) return COSMOS_EALIGN;
-  if (id->kind < 0 || id->kind > 2) return COSMOS_EINVAL;
+  if (id->kind < 0 || id->kind > 3) return COSMOS_EINVAL;
   if (id->kind == 0 && p->fluid) return COSMOS_EINVAL;                   // the gauge wave is vacuum
   if (id->kind == 2 && (!p->fluid || !p->scalar)) return COSMOS_EINVAL;  // isocurvature: scalar + fluid
+  if (id->kind == 3 && (!p->fluid || !(p->H0 > 0.0))) return COSMOS_EINVAL;  // next order: fluid, background
   if (id->kind >= 1 && (!(id->sigma > 0.0) || !(id->a0 > 0.0) || !(id->q[0] > 0.0) || !(id->q[1] > 0.0) ||
                         !(id->q[2] > 0.0)))
     return COSMOS_EINVAL;
@@ -405,6 +406,10 @@ int init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id,
   a.Lx = Lx_wave > 0.0 ? Lx_wave : g->nx * g->h[0];
   init_metric_kernel<<<point_grid(a.g), dim3(BX, BY), 0, s>>>(a, state);
   CK(cudaGetLastError());
+  if (id->kind == 3) {
+    double* w = (double*)ws;
+    return init_nlo(g, p, state, w + L.hm, w + L.partial, s);
+  }
   if (need_ws) {
     double* w = (double*)ws;
     ConstraintArgs c;

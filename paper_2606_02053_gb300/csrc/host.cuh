@@ -25,5 +25,10 @@ int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const doub
 int init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,
               size_t ws_bytes, cudaStream_t s, double Lx_wave);
 int cuda_error(cudaError_t e);  // records e for cosmos_last_cuda_error; returns COSMOS_ECUDA
+// Id kind 3 (init_nlo.cu): from the leading-order FLRW + zeta metric in `state`,
+// the next-to-leading-order metric, Gt and the fluid's E, J_i; hm (4 fields)
+// and partial (constraint-kernel partials) are scratch.
+int init_nlo(const cosmos_grid* g, const cosmos_params* p, double* state, double* hm, double* partial,
+             cudaStream_t s);
 
 }  // namespace cosmos
