@@ -108,6 +108,7 @@ def parse():
     ap.add_argument("--grid", type=int, default=N_GRID, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-extras", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--state", default="gauge", choices=["gauge", "generic"], help=argparse.SUPPRESS)
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "scan", "adjoint", "flrw", "fmr", "isocurvature", "mode"],
                     help="sweep: single 256^3 grid (headline); scan: 64-instance batched threshold scan; "
@@ -747,6 +748,10 @@ def main():
     ev = Evolution(g, p, device=f"cuda:{local}")
     ev.init(C.make_id(0, A=0.01))
     host_gauge_wave = ev.get() if rank == 0 and not args.no_cpu_baseline else None
+    if args.state == "generic":  # profiling only: the same sweep on the generic state of sweep_generic
+        from paper_2606_02053_gb300 import inputs
+
+        ev.set_state(inputs.smooth_state(n, seed=2562, kmax=6, scale=0.5))
     U1 = torch.empty_like(ev.state)
     U2 = torch.empty_like(ev.state)
     acc = torch.empty_like(ev.state)
