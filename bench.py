@@ -109,6 +109,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-extras", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--state", default="gauge", choices=["gauge", "generic"], help=argparse.SUPPRESS)
+    ap.add_argument("--decompose", action="store_true",
+                    help="hold the 256^3 grid as one z-slab per rank (ghost-plane exchange every RK4 stage; "
+                         "strong scaling) instead of one whole grid per rank")
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "scan", "adjoint", "flrw", "fmr", "isocurvature", "mode"],
                     help="sweep: single 256^3 grid (headline); scan: 64-instance batched threshold scan; "
@@ -705,10 +708,76 @@ def adjoint_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def decomposed_workload(args):
+    """The headline gauge wave held as z-slabs, one per rank (strong scaling): before
+    every RK4 stage the ranks exchange 3 ghost planes with their two neighbours
+    (periodic) and take the largest per-field exponent (NCCL); each rank advances its
+    own planes with cosmos_rk4_stage_slab.  With one rank the slab's ghost planes come
+    from its own planes.  Bitwise the whole-grid results (tests/test_gpu_slab.py)."""
+    import torch
+
+    from paper_2606_02053_gb300 import build
+    from paper_2606_02053_gb300 import cosmos as C
+    from paper_2606_02053_gb300.dist import max_over_ranks
+    from paper_2606_02053_gb300.slab import DistExchange, LocalExchange, Slab, SlabEvolution, slab_bounds
+
+    ws_, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws_ > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    if rank == 0:
+        build.build()
+    if ws_ > 1:
+        tdist.barrier()
+    n = args.grid
+    h = 1.0 / n
+    dt = 0.25 * h
+    p = C.make_params(slicing=0, shift=1, eta=2.0, ko_sigma=0.1)
+    k0, k1 = slab_bounds(n, ws_)[rank]
+    slab = Slab((n, n, n), (h, h, h), (0.0, 0.0, 0.0), p, k0, k1, device=f"cuda:{local}")
+    # the gauge wave depends on x alone: every plane of the slab, ghosts included, is the whole grid's
+    C.check(C.cosmos_init_grid(slab.g, p, C.make_id(0, A=0.01), slab.state, None))
+    evo = SlabEvolution([slab], DistExchange() if ws_ > 1 else LocalExchange())
+    evo.step(0.0, dt, steps=args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    if ws_ > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    evo.step(args.warmup * dt, dt, steps=args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    if ws_ > 1:
+        tdist.barrier()
+    clk = clocks.stop()
+    elapsed = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": float(n) ** 3 * args.steps / elapsed, "unit": UNIT, "n_gpus": ws_,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": n, "fields": STATE_FIELDS, "dt_over_h": 0.25,
+                           "parallelism": f"z-slabs x{ws_} (3 ghost planes a side, exchange every stage)",
+                           "l2": "inputs larger than L2 (3.2 GB state per level)"},
+                "gpu_launches": 16 * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        tdist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.decompose:
+        return decomposed_workload(args)
     if args.workload == "scan":
         return scan_workload(args)
     if args.workload == "adjoint":

@@ -177,6 +177,41 @@ int cosmos_rhs(const cosmos_grid* g, const cosmos_params* p, const double* state
 int cosmos_rk4_stage(const cosmos_grid* g, const cosmos_params* p, int stage, const double* U_s, double* U_n,
                      double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Slab decomposition of one grid over several ranks (one GPU each): every
+ * rank holds a slab of z-planes plus 3 ghost planes on each side (the reach
+ * of the Kreiss-Oliger stencil), as an ordinary grid of nz_slab + 6 planes.
+ * Before each RK4 stage the ranks exchange the ghost planes of the stage
+ * state (periodic in z across the ranks) and take the largest of their
+ * per-field exponents (cosmos_field_exponents), so that the integer
+ * derivative pass rounds exactly as on the whole grid; cosmos_rk4_stage_slab
+ * then advances the slab's interior planes.  The results equal the single-
+ * grid ones bitwise.  The paper's code runs on one node with OpenMP; this is
+ * the GPU form of its grid's natural split.
+ * ------------------------------------------------------------------------ */
+
+/* E[s] = the largest biased FP64 exponent over the whole array of limb slot
+ * s (slot s = field s; with the fluid on, the scalar's fields move down by 4:
+ * 24 + 2 scalar slots), the reference exponent of the integer derivative
+ * pass.  E: device memory, 24 + 2 * scalar ints.  Asynchronous. */
+int cosmos_field_exponents(const cosmos_grid* g, const cosmos_params* p, const double* state, int* E,
+                           void* stream);
+
+/* cosmos_rk4_stage with the algebra pass and the stage combine restricted to
+ * planes k_lo .. k_lo + k_cnt - 1 (the derivative and fluid passes cover
+ * every plane, so planes within 3 of the range must hold the right values:
+ * the ghost planes of a slab), and, if E is not NULL, the derivative pass's
+ * reference exponents taken from E (device, as cosmos_field_exponents
+ * writes it) instead of its own scan of U_s.  Every entry of E must be at
+ * least the exponent cosmos_field_exponents gives for U_s itself (the
+ * largest over all ranks is): a smaller one overflows the fixed-point copy
+ * and gives wrong derivatives (no fault).  Planes outside the range of U_next
+ * / U_n / acc are not written.  ws: COSMOS_OP_RHS bytes.  Errors as
+ * cosmos_rk4_stage, and COSMOS_EINVAL for a range outside 0..nz. */
+int cosmos_rk4_stage_slab(const cosmos_grid* g, const cosmos_params* p, int stage, const double* U_s, double* U_n,
+                          double* U_next, double* acc, double t, double dt, int k_lo, int k_cnt, const int* E,
+                          void* ws, size_t ws_bytes, void* stream);
+
 /* One pass of a fused RK4 stage (arguments as cosmos_rk4_stage), so that
  * the passes can be scheduled or timed separately:
  *   pass 0: fluid primitives and face fluxes of U_s (nothing without fluid)

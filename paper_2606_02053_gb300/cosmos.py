@@ -83,6 +83,9 @@ _SIGS = {
     "cosmos_rk4_stage": ([_G, _PP, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_rk4_step": ([_G, _PP, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_rk4_step_stages": ([_G, _PP, _P, _D, _D, _P, _P, _P, _P, _S, _P], ctypes.c_int),
+    "cosmos_field_exponents": ([_G, _PP, _P, _P, _P], ctypes.c_int),
+    "cosmos_rk4_stage_slab": ([_G, _PP, ctypes.c_int, _P, _P, _P, _P, _D, _D, ctypes.c_int, ctypes.c_int, _P, _P, _S,
+                               _P], ctypes.c_int),
     "cosmos_stage_pass": ([_G, _PP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
@@ -198,6 +201,18 @@ def cosmos_rk4_stage(g, p, stage, U_s, U_n, U_next, acc, t, dt, ws=None, stream=
     w, nb = _ws(ws)
     return lib().cosmos_rk4_stage(ctypes.byref(g), ctypes.byref(p), int(stage), _ptr(U_s), _ptr(U_n), _ptr(U_next),
                                   _ptr(acc), float(t), float(dt), w, nb, _stream(stream))
+
+
+def cosmos_field_exponents(g, p, state, E, stream=None) -> int:
+    return lib().cosmos_field_exponents(ctypes.byref(g), ctypes.byref(p), _ptr(state), _ptr(E), _stream(stream))
+
+
+def cosmos_rk4_stage_slab(g, p, stage, U_s, U_n, U_next, acc, t, dt, k_lo, k_cnt, E=None, ws=None,
+                          stream=None) -> int:
+    w, nb = _ws(ws)
+    return lib().cosmos_rk4_stage_slab(ctypes.byref(g), ctypes.byref(p), int(stage), _ptr(U_s), _ptr(U_n),
+                                       _ptr(U_next), _ptr(acc), float(t), float(dt), int(k_lo), int(k_cnt), _ptr(E),
+                                       w, nb, _stream(stream))
 
 
 def cosmos_stage_pass(g, p, pss, stage, U_s, U_n, U_next, acc, t, dt, ws=None, stream=None) -> int:

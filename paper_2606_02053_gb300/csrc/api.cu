@@ -320,7 +320,7 @@ static ConstraintLauncher constraint_launcher(const cosmos_params* p) {
 // k_lo, k_cnt: plane range of the algebra pass (k_cnt = 0: all planes).
 int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n, double* out,
               double* acc, double t_stage, double cdt, double bk, double* ws, const WsLayout& L, cudaStream_t s,
-              int pass_mask, int f_lo, int f_hi, int k_lo, int k_cnt) {
+              int pass_mask, int f_lo, int f_hi, int k_lo, int k_cnt, const int* E_ext) {
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.f_lo = f_lo;
@@ -360,7 +360,12 @@ int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const doub
       s_lo = sl < s_lo ? sl : s_lo;
       s_hi = sl + 1 > s_hi ? sl + 1 : s_hi;
     }
-    CK(launch_limbs(a.g, U_s, p->fluid, s_lo, s_hi, (int*)(ws + L.expo), (long long*)(ws + L.limbs), s));
+    if (E_ext) {
+      a.E = E_ext;
+      CK(launch_to_limbs(a.g, U_s, p->fluid, s_lo, s_hi, E_ext, (long long*)(ws + L.limbs), s));
+    } else {
+      CK(launch_limbs(a.g, U_s, p->fluid, s_lo, s_hi, (int*)(ws + L.expo), (long long*)(ws + L.limbs), s));
+    }
   }
   if ((pass_mask & 6) == 6) {
     CK(stage_launcher(p)(a, mode, s));
@@ -485,6 +490,36 @@ int cosmos_rk4_stage(const cosmos_grid* g, const cosmos_params* p, int stage, co
   const double cdt = stage == 1 || stage == 2 ? 0.5 * dt : (stage == 3 ? dt : dt / 6.0);
   return run_stage(g, p, modes[stage - 1], U_s, U_n, U_next, acc, t + c_stage[stage - 1] * dt, cdt, 2.0,
                    (double*)ws, L, (cudaStream_t)stream);
+}
+
+int cosmos_field_exponents(const cosmos_grid* g, const cosmos_params* p, const double* state, int* E,
+                           void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state || !E) return COSMOS_EINVAL;
+  const int nslot = 24 + 2 * p->scalar;
+  CK(launch_field_exponents(make_devgrid(g), state, p->fluid, 0, nslot, E, (cudaStream_t)stream));
+  return COSMOS_OK;
+}
+
+int cosmos_rk4_stage_slab(const cosmos_grid* g, const cosmos_params* p, int stage, const double* U_s, double* U_n,
+                          double* U_next, double* acc, double t, double dt, int k_lo, int k_cnt, const int* E,
+                          void* ws, size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (stage < 1 || stage > 4 || !U_s || !U_n || !acc) return COSMOS_EINVAL;
+  if (stage < 4 && !U_next) return COSMOS_EINVAL;
+  if (U_s == acc || (stage < 4 && (U_s == U_next || U_next == acc || U_next == U_n))) return COSMOS_EINVAL;
+  if (stage == 4 && U_s == U_n) return COSMOS_EINVAL;
+  if (k_lo < 0 || k_cnt < 1 || k_lo + k_cnt > g->nz) return COSMOS_EINVAL;
+  if (!aligned16(U_s) || !aligned16(U_n) || !aligned16(acc) || (U_next && !aligned16(U_next))) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RHS);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
+  static const int modes[4] = {MODE_S1, MODE_S23, MODE_S23, MODE_S4};
+  const double cdt = stage == 1 || stage == 2 ? 0.5 * dt : (stage == 3 ? dt : dt / 6.0);
+  return run_stage(g, p, modes[stage - 1], U_s, U_n, U_next, acc, t + c_stage[stage - 1] * dt, cdt, 2.0,
+                   (double*)ws, L, (cudaStream_t)stream, 7, 0, 0, k_lo, k_cnt, E);
 }
 
 int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, int stage, const double* U_s,

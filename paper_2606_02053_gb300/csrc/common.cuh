@@ -162,6 +162,11 @@ cudaError_t launch_init_zeta_vjp(const DevGrid& g, const Coef& c, const AlgebraP
 // (slot s = field s, or s + 4 past the fluid fields when the fluid is on)
 cudaError_t launch_limbs(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, int* E, long long* L,
                          cudaStream_t s);
+// the limb copy with given exponents E (no scan); the exponent scan alone
+cudaError_t launch_to_limbs(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, const int* E,
+                            long long* L, cudaStream_t s);
+cudaError_t launch_field_exponents(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, int* E,
+                                   cudaStream_t s);
 // the same for every instance of a batch (args[i] = instance i's stage arguments;
 // E_all = the n x nslot exponents, contiguous, args[i].E = E_all + i nslot)
 cudaError_t launch_batch_limbs(const StageArgs* args, int n, int nslot, int fluid, int* E_all, cudaStream_t s);

@@ -16,10 +16,13 @@ int check_ws(const WsLayout& L, void* ws, size_t ws_bytes);  // COSMOS_OK, EINVA
 bool aligned16(const void* p);
 // One RK4 stage (or one of its passes) of one grid, as cosmos_rk4_stage runs it
 // (api.cu): pass_mask bit 0 fluid pre-pass, bit 1 derivative pass, bit 2
-// algebra pass + combine; f_lo/f_hi and k_lo/k_cnt restrict the passes.
+// algebra pass + combine; f_lo/f_hi and k_lo/k_cnt restrict the passes;
+// E_ext (device, one int per limb slot), if given, replaces the exponent scan
+// of the limb copy.
 int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n, double* out,
               double* acc, double t_stage, double cdt, double bk, double* ws, const WsLayout& L, cudaStream_t s,
-              int pass_mask = 7, int f_lo = 0, int f_hi = 0, int k_lo = 0, int k_cnt = 0);
+              int pass_mask = 7, int f_lo = 0, int f_hi = 0, int k_lo = 0, int k_cnt = 0,
+              const int* E_ext = nullptr);
 // cosmos_init_grid with the gauge wave's wavelength given (Lx_wave > 0) instead
 // of the grid's own length nx h_x.
 int init_grid(const cosmos_grid* g, const cosmos_params* p, const cosmos_id* id, double* state, void* ws,

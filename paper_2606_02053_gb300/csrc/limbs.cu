@@ -107,4 +107,29 @@ cudaError_t launch_limbs(const DevGrid& g, const double* U, int fluid, int s_lo,
   return cudaGetLastError();
 }
 
+// The limb copy of slots s_lo .. s_hi - 1 with the reference exponents given
+// in E (no scan).
+cudaError_t launch_to_limbs(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, const int* E,
+                            long long* L, cudaStream_t s) {
+  if (s_hi <= s_lo) return cudaSuccess;
+  const long rows = (long)g.ny * g.nz;
+  const int threads = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64);
+  const dim3 grid((unsigned)(rows < 2048 ? rows : 2048), (unsigned)(s_hi - s_lo));
+  to_limbs_kernel<<<grid, threads, 0, s>>>(g, U, s_lo, fluid, E, L);
+  return cudaGetLastError();
+}
+
+// Only the exponent scan of slots s_lo .. s_hi - 1 into E.
+cudaError_t launch_field_exponents(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, int* E,
+                                   cudaStream_t s) {
+  if (s_hi <= s_lo) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(E + s_lo, 0, sizeof(int) * (s_hi - s_lo), s);
+  if (e != cudaSuccess) return e;
+  const long rows = (long)g.ny * g.nz;
+  const int threads = g.nx >= 256 ? 256 : (g.nx >= 128 ? 128 : 64);
+  const dim3 grid((unsigned)(rows < 2048 ? rows : 2048), (unsigned)(s_hi - s_lo));
+  field_exponent_kernel<<<grid, threads, 0, s>>>(g, U, s_lo, fluid, E);
+  return cudaGetLastError();
+}
+
 }  // namespace cosmos

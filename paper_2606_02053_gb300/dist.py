@@ -1,9 +1,9 @@
 """Host-side logic for running on several GPUs of one node.
 
-The sweep itself is not decomposed across GPUs here (every run of this
-library uses one GPU per process); with N processes each rank evolves its
-own grid or its own share of a batched scan.  The only cross-rank traffic is
-timing and bookkeeping: no collective touches the evolved data.
+With N processes each rank evolves its own grid (replicas) or its own share
+of a batched scan (independent instances: no collective touches the evolved
+data), or holds one z-slab of a single grid (slab.py: the ghost-plane
+exchange and the exponent reduction are the only collectives).
 
 * ``shard_instances``: contiguous, balanced split of scan instances by their
   point count (greedy over ranks, deterministic).
