@@ -831,15 +831,21 @@ def main():
     acc = torch.empty_like(ev.state)
     stream = torch.cuda.current_stream()
 
+    # pass options as cosmos_rk4_step uses them: the algebra pass of stages 1-3 records the exponents
+    # of the state it writes (+32, stage 1 clearing the record first: +64), the derivative pass of
+    # stages 2-4 takes them instead of scanning (+16)
+    pass_opts = {(1, 1): 0, (1, 2): 32 + 64, (2, 1): 16, (2, 2): 32, (3, 1): 16, (3, 2): 32, (4, 1): 16, (4, 2): 0}
+
     def stage_calls(t, events=None):
-        """One RK4 step as 4 stages x (derivative pass, algebra pass); events
-        bracket each pass on the launching stream."""
+        """One RK4 step as 4 stages x (derivative pass, algebra pass), the sequence of
+        cosmos_rk4_step; events bracket each pass on the launching stream."""
         seq = [(ev.state, U1), (U1, U2), (U2, U1), (U1, None)]
         for s, (src, dst) in enumerate(seq, start=1):
             for pss in (1, 2):
                 if events is not None:
                     events[s - 1][pss - 1][0].record(stream)
-                C.check(C.cosmos_stage_pass(g, p, pss, s, src, ev.state, dst, acc, t, dt, ev.ws_rhs, stream))
+                C.check(C.cosmos_stage_pass(g, p, pss + pass_opts[(s, pss)], s, src, ev.state, dst, acc, t, dt,
+                                            ev.ws_rhs, stream))
                 if events is not None:
                     events[s - 1][pss - 1][1].record(stream)
 
@@ -874,7 +880,9 @@ def main():
     nranks = ws_
     pts = float(n) ** 3
     value = nranks * pts * args.steps / elapsed
-    gpu_launches = 16 * args.steps  # per stage: exponent scan, limb copy, integer derivative pass, algebra pass
+    # per step: exponent scan (stage 1), 4 x (limb copy, integer derivative pass, algebra pass),
+    # exponent record compaction (stages 1-3)
+    gpu_launches = 16 * args.steps
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     nbytes = ev.state.numel() * 8

@@ -218,7 +218,16 @@ int cosmos_rk4_stage_slab(const cosmos_grid* g, const cosmos_params* p, int stag
  *   pass 1: derivative pass: finite differences and Kreiss-Oliger terms of U_s
  *   pass 2: algebra pass + stage combine (needs passes 0 and 1 of this stage)
  * Passes 0, 1, 2 in order equal one cosmos_rk4_stage call.  The workspace
- * carries the intermediate results between passes. */
+ * carries the intermediate results between passes.  Option bits added to
+ * `pass` reproduce what cosmos_rk4_step does between its stages:
+ *   + 32 (pass 2, stages 1-3): the algebra pass records the largest FP64
+ *        exponent of every field it writes to U_next into the workspace
+ *        (+ 64: the same, clearing the record first: needed once per
+ *        workspace before its first record);
+ *   + 16 (pass 1): the derivative pass takes those recorded exponents
+ *        instead of scanning U_s, which must then be the U_next of the
+ *        recording pass, unchanged since.
+ * Results are bitwise those without the options (the same maxima). */
 int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, int stage, const double* U_s,
                       double* U_n, double* U_next, double* acc, double t, double dt, void* ws, size_t ws_bytes,
                       void* stream);
@@ -227,8 +236,10 @@ int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, in
  * section "Physical system settings" (the right-hand side of cosmos_rhs),
  * in place on `state`: k_s = F(U_s, t + c_s dt), U_{n+1} = U_n + dt/6
  * (k1 + 2 k2 + 2 k3 + k4), as four cosmos_rk4_stage calls, each fused with
- * its stage combine.  ws: COSMOS_OP_RK4 bytes (two stage buffers, the
- * accumulator and the fluid buffers).  Errors as cosmos_rhs. */
+ * its stage combine (stages 2-4 take their fields' largest exponents as the
+ * algebra pass of the stage before records them, instead of a scan of the
+ * state: bitwise the same).  ws: COSMOS_OP_RK4 bytes (two stage buffers,
+ * the accumulator and the fluid buffers).  Errors as cosmos_rhs. */
 int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
                     size_t ws_bytes, void* stream);
 

@@ -122,6 +122,7 @@ WsLayout ws_layout(const cosmos_grid* g, const cosmos_params* p, int op) {
     const int nslot = 24 + 2 * p->scalar;
     L.limbs = take((size_t)nslot * fs);
     L.expo = take(((size_t)nslot + 1) / 2);
+    L.erec = take(16 * (size_t)nslot);  // 32 unsigned per slot, one cache line each
     if (op == COSMOS_OP_RK4) {
       L.stageA = take(nf * fs);
       L.stageB = take(nf * fs);
@@ -320,7 +321,7 @@ static ConstraintLauncher constraint_launcher(const cosmos_params* p) {
 // k_lo, k_cnt: plane range of the algebra pass (k_cnt = 0: all planes).
 int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const double* U_s, double* U_n, double* out,
               double* acc, double t_stage, double cdt, double bk, double* ws, const WsLayout& L, cudaStream_t s,
-              int pass_mask, int f_lo, int f_hi, int k_lo, int k_cnt, const int* E_ext) {
+              int pass_mask, int f_lo, int f_hi, int k_lo, int k_cnt, const int* E_ext, int expo_flags) {
   StageArgs a;
   memset(&a, 0, sizeof(a));
   a.f_lo = f_lo;
@@ -363,9 +364,16 @@ int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const doub
     if (E_ext) {
       a.E = E_ext;
       CK(launch_to_limbs(a.g, U_s, p->fluid, s_lo, s_hi, E_ext, (long long*)(ws + L.limbs), s));
+    } else if (expo_flags & 1) {  // exponents recorded by the previous stage's algebra pass
+      CK(launch_to_limbs(a.g, U_s, p->fluid, s_lo, s_hi, a.E, (long long*)(ws + L.limbs), s));
     } else {
       CK(launch_limbs(a.g, U_s, p->fluid, s_lo, s_hi, (int*)(ws + L.expo), (long long*)(ws + L.limbs), s));
     }
+  }
+  const int nslot = 24 + 2 * p->scalar;
+  if (expo_flags & 2) {
+    a.E_rec = (unsigned*)(ws + L.erec);
+    if (expo_flags & 4) CK(cudaMemsetAsync(a.E_rec, 0, sizeof(unsigned) * 32 * nslot, s));
   }
   if ((pass_mask & 6) == 6) {
     CK(stage_launcher(p)(a, mode, s));
@@ -374,6 +382,7 @@ int run_stage(const cosmos_grid* g, const cosmos_params* p, int mode, const doub
   } else if (pass_mask & 4) {
     CK(stage_launcher(p)(a, mode | 8, s));  // algebra pass only
   }
+  if ((expo_flags & 2) && (pass_mask & 4)) CK(launch_exponents_from_record(a.E_rec, (int*)(ws + L.expo), nslot, s));
   return COSMOS_OK;
 }
 
@@ -527,7 +536,10 @@ int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, in
                       void* stream) {
   int e = validate(g, p);
   if (e) return e;
-  if (pass < 0 || pass > 2 || stage < 1 || stage > 4 || !U_s || !U_n || !acc) return COSMOS_EINVAL;
+  const int opts = pass & ~3;
+  pass &= 3;
+  if (pass > 2 || (opts & ~(16 | 32 | 64)) || stage < 1 || stage > 4 || !U_s || !U_n || !acc) return COSMOS_EINVAL;
+  if (((opts & 16) && pass != 1) || ((opts & (32 | 64)) && (pass != 2 || stage == 4))) return COSMOS_EINVAL;
   if (stage < 4 && !U_next) return COSMOS_EINVAL;
   if (U_s == acc || (stage < 4 && (U_s == U_next || U_next == acc || U_next == U_n))) return COSMOS_EINVAL;
   if (stage == 4 && U_s == U_n) return COSMOS_EINVAL;
@@ -536,8 +548,9 @@ int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, in
   static const double c_stage[4] = {0.0, 0.5, 0.5, 1.0};
   static const int modes[4] = {MODE_S1, MODE_S23, MODE_S23, MODE_S4};
   const double cdt = stage == 1 || stage == 2 ? 0.5 * dt : (stage == 3 ? dt : dt / 6.0);
+  const int expo_flags = ((opts & 16) ? 1 : 0) | ((opts & 32) ? 2 : 0) | ((opts & 64) ? 6 : 0);
   return run_stage(g, p, modes[stage - 1], U_s, U_n, U_next, acc, t + c_stage[stage - 1] * dt, cdt, 2.0,
-                   (double*)ws, L, (cudaStream_t)stream, 1 << pass);
+                   (double*)ws, L, (cudaStream_t)stream, 1 << pass, 0, 0, 0, 0, nullptr, expo_flags);
 }
 
 int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
@@ -554,10 +567,14 @@ int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state,
   double* acc = w + L.acc;
   cudaStream_t s = (cudaStream_t)stream;
   const double dt2 = 0.5 * dt;
-  if ((e = run_stage(g, p, MODE_S1, state, state, A, acc, t, dt2, 2.0, w, L, s))) return e;
-  if ((e = run_stage(g, p, MODE_S23, A, state, B, acc, t + dt2, dt2, 2.0, w, L, s))) return e;
-  if ((e = run_stage(g, p, MODE_S23, B, state, A, acc, t + dt2, dt, 2.0, w, L, s))) return e;
-  return run_stage(g, p, MODE_S4, A, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s);
+  // stage 1 scans U_n (the caller may have changed it); each algebra pass records the
+  // exponents of the state it writes, so stages 2-4 need no scan
+  if ((e = run_stage(g, p, MODE_S1, state, state, A, acc, t, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 6))) return e;
+  if ((e = run_stage(g, p, MODE_S23, A, state, B, acc, t + dt2, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
+    return e;
+  if ((e = run_stage(g, p, MODE_S23, B, state, A, acc, t + dt2, dt, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
+    return e;
+  return run_stage(g, p, MODE_S4, A, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 1);
 }
 
 int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt,
@@ -574,10 +591,12 @@ int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double*
   cudaStream_t s = (cudaStream_t)stream;
   const double dt2 = 0.5 * dt;
   // the stages of cosmos_rk4_step, with the stage states kept in U2, U3, U4
-  if ((e = run_stage(g, p, MODE_S1, state, state, U2, acc, t, dt2, 2.0, w, L, s))) return e;
-  if ((e = run_stage(g, p, MODE_S23, U2, state, U3, acc, t + dt2, dt2, 2.0, w, L, s))) return e;
-  if ((e = run_stage(g, p, MODE_S23, U3, state, U4, acc, t + dt2, dt, 2.0, w, L, s))) return e;
-  return run_stage(g, p, MODE_S4, U4, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s);
+  if ((e = run_stage(g, p, MODE_S1, state, state, U2, acc, t, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 6))) return e;
+  if ((e = run_stage(g, p, MODE_S23, U2, state, U3, acc, t + dt2, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
+    return e;
+  if ((e = run_stage(g, p, MODE_S23, U3, state, U4, acc, t + dt2, dt, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
+    return e;
+  return run_stage(g, p, MODE_S4, U4, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 1);
 }
 
 namespace {

@@ -96,6 +96,8 @@ struct StageArgs {
   int skip_ko;                     // derivative pass: leave the Kreiss-Oliger slots of D unwritten
   const long long* __restrict__ L; // limb copy of U (stage_int.cuh); null: the FP64 derivative pass
   const int* __restrict__ E;       // reference exponent of each limb slot
+  unsigned* E_rec;                 // algebra pass, stages 1-3: records the largest biased exponent of
+                                   // each limb slot of U_next at E_rec[32 slot] (null: no record)
 };
 
 // Doubles per point of the derivative-pass buffer: first and second
@@ -167,6 +169,8 @@ cudaError_t launch_to_limbs(const DevGrid& g, const double* U, int fluid, int s_
                             long long* L, cudaStream_t s);
 cudaError_t launch_field_exponents(const DevGrid& g, const double* U, int fluid, int s_lo, int s_hi, int* E,
                                    cudaStream_t s);
+// E[s] = rec[32 s] and rec[32 s] = 0 for s < nslot (the exponents an algebra pass recorded)
+cudaError_t launch_exponents_from_record(unsigned* rec, int* E, int nslot, cudaStream_t s);
 // the same for every instance of a batch (args[i] = instance i's stage arguments;
 // E_all = the n x nslot exponents, contiguous, args[i].E = E_all + i nslot)
 cudaError_t launch_batch_limbs(const StageArgs* args, int n, int nslot, int fluid, int* E_all, cudaStream_t s);

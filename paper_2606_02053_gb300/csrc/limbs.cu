@@ -132,4 +132,17 @@ cudaError_t launch_field_exponents(const DevGrid& g, const double* U, int fluid,
   return cudaGetLastError();
 }
 
+__global__ void exponents_from_record_kernel(unsigned* __restrict__ rec, int* __restrict__ E, int nslot) {
+  const int s = threadIdx.x;
+  if (s < nslot) {
+    E[s] = (int)rec[32 * s];
+    rec[32 * s] = 0u;
+  }
+}
+
+cudaError_t launch_exponents_from_record(unsigned* rec, int* E, int nslot, cudaStream_t s) {
+  exponents_from_record_kernel<<<1, 32, 0, s>>>(rec, E, nslot);
+  return cudaGetLastError();
+}
+
 }  // namespace cosmos

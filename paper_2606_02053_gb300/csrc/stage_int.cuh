@@ -85,6 +85,26 @@ __device__ __forceinline__ double round_mag(unsigned long long uh, unsigned long
   return __longlong_as_double((long long)bits);
 }
 
+// round_mag for a magnitude below 2^63 (uh = 0), bitwise the same: round to
+// nearest even by adding half a unit of the last kept place less one plus the
+// kept part's lowest bit and truncating (no overflow: lo < 2^63); the leading
+// one, or a carry out of the significand, adds into the exponent field.
+__device__ __forceinline__ double round_mag64(unsigned long long lo, bool neg, int e_ref) {
+  if (lo == 0) return 0.0;
+  const int n = 63 - __clzll(lo);
+  const int ex = n + e_ref - 1085 + 1023;  // biased exponent of the leading one
+  unsigned long long m;
+  if (n <= 52) {
+    m = lo << (52 - n);
+  } else {
+    const int r = n - 52;
+    m = (lo + ((1ull << (r - 1)) - 1ull) + ((lo >> r) & 1ull)) >> r;
+  }
+  const long long b = ((long long)(ex - 1) << 52) + (long long)m;  // m in [2^52, 2^53]
+  if ((b >> 52) <= 0) return neg ? -0.0 : 0.0;  // below the normal range (as round_mag)
+  return __longlong_as_double((long long)((unsigned long long)b | ((unsigned long long)neg << 63)));
+}
+
 // FP64 value of the digit sums S.x + S.y 2^21 + S.z 2^42 (|S.k| < 2^31) in the
 // units of a field with reference exponent e_ref.
 __device__ __forceinline__ double from_limbs(int3 S, int e_ref) {
@@ -93,7 +113,7 @@ __device__ __forceinline__ double from_limbs(int3 S, int e_ref) {
   if (S.z < (1 << 20) && S.z > -(1 << 20)) {                            // |value| < 2^63: one 64-bit word
     const long long v = t1 + ((long long)S.z << 42);
     const bool neg = v < 0;
-    return round_mag(0ull, neg ? (unsigned long long)(-v) : (unsigned long long)v, neg, e_ref);
+    return round_mag64(neg ? (unsigned long long)(-v) : (unsigned long long)v, neg, e_ref);
   }
   // value = t1 + S.z 2^42 as a signed 128-bit integer (hi, lo)
   const unsigned long long p = (unsigned long long)((long long)S.z << 42);

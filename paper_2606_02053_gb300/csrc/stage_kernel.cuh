@@ -194,6 +194,18 @@ struct AlgIn {
   }
 };
 
+// The largest biased exponent of v over the warp's active lanes into *E (one
+// atomic per warp): the next stage's reference exponent without a scan of the
+// state (the exponent field of the stored value, as field_exponent_kernel reads).
+__device__ __forceinline__ void record_exponent(unsigned* E, double v) {
+  const unsigned e = (unsigned)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu);
+  const unsigned mask = __activemask();
+  const unsigned m = __reduce_max_sync(mask, e);
+  unsigned lane;
+  asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+  if (lane == (unsigned)(__ffs(mask) - 1)) atomicMax(E, m);
+}
+
 // Output side of the algebra pass: out[f] = r adds the Kreiss-Oliger term (or
 // the fluid flux divergence) and applies the RK4 stage combine of MODE, as
 // soon as the generated code has the value.
@@ -221,11 +233,15 @@ struct AlgOut {
       if constexpr (MODE == MODE_RHS) {
         a.out[ofs] = r;
       } else if constexpr (MODE == MODE_S1) {
-        a.out[ofs] = fma(a.cdt, r, ldg(a.U0, ofs));
+        const double v = fma(a.cdt, r, ldg(a.U0, ofs));
+        a.out[ofs] = v;
         a.acc[ofs] = r;
+        if (a.E_rec && !(T::FLUID && f >= 24 && f < 28)) record_exponent(a.E_rec + 32 * ko_slot<T>(f), v);
       } else if constexpr (MODE == MODE_S23) {
-        a.out[ofs] = fma(a.cdt, r, ldg(a.U0, ofs));
+        const double v = fma(a.cdt, r, ldg(a.U0, ofs));
+        a.out[ofs] = v;
         a.acc[ofs] = fma(a.bk, r, a.acc[ofs]);
+        if (a.E_rec && !(T::FLUID && f >= 24 && f < 28)) record_exponent(a.E_rec + 32 * ko_slot<T>(f), v);
       } else {
         a.U0w[ofs] = fma(a.cdt, a.acc[ofs] + r, a.U0w[ofs]);
       }

@@ -144,25 +144,43 @@ def test_rk4_step_parity(C, O, fluid):
     assert field_errors(ev.get(), ref).max() <= STEP_TOL
 
 
-def test_rk4_stage_entry_point_composes_to_step(C):
-    """Four cosmos_rk4_stage calls equal one cosmos_rk4_step, bitwise."""
+@pytest.mark.parametrize("fluid,scalar,n,pitch", [(0, 0, (16, 16, 16), None), (1, 1, (21, 11, 13), 24),
+                                                   (0, 0, (37, 9, 12), 40)])
+def test_rk4_stage_entry_point_composes_to_step(C, fluid, scalar, n, pitch):
+    """Four cosmos_rk4_stage calls (each scanning its stage state for the integer
+    pass's exponents) equal one cosmos_rk4_step (stages 2-4 taking the exponents the
+    previous algebra pass recorded), bitwise; so does the per-pass sequence with the
+    record options, on ragged rows whose last warp is partly idle."""
     from paper_2606_02053_gb300 import inputs
     from paper_2606_02053_gb300.evolve import Evolution
 
-    n = (16, 16, 16)
-    h = 1.0 / 16
-    p = C.make_params()
-    s = inputs.smooth_state(n, seed=4)
-    a = Evolution(C.make_grid(n, h), p)
+    h = 1.0 / n[0]
+    p = C.make_params(fluid=fluid, scalar=scalar, H0=2.0 * fluid)
+    s = inputs.smooth_state(n, seed=4, fluid=fluid, scalar=scalar, scale=0.5)
+    a = Evolution(C.make_grid(n, h, pitch=pitch), p)
     a.set_state(s)
     a.step(0.0, 0.01)
-    b = Evolution(C.make_grid(n, h), p)
-    b.set_state(s)
-    U1, U2, acc = (torch.empty_like(b.state) for _ in range(3))
-    ws = b.ws_rhs
-    for st, (src, dst) in enumerate([(b.state, U1), (U1, U2), (U2, U1), (U1, None)], start=1):
-        C.check(C.cosmos_rk4_stage(b.g, b.p, st, src, b.state, dst, acc, 0.0, 0.01, ws))
-    assert torch.equal(a.state, b.state)
+    for options in (False, True):
+        b = Evolution(C.make_grid(n, h, pitch=pitch), p)
+        b.set_state(s)
+        U1, U2, acc = (torch.empty_like(b.state) for _ in range(3))
+        ws = b.ws_rhs
+        opts = {(1, 1): 0, (1, 2): 96, (2, 1): 16, (2, 2): 32, (3, 1): 16, (3, 2): 32, (4, 1): 16, (4, 2): 0}
+        for st, (src, dst) in enumerate([(b.state, U1), (U1, U2), (U2, U1), (U1, None)], start=1):
+            if options:
+                for pss in (0, 1, 2):
+                    C.check(C.cosmos_stage_pass(b.g, b.p, pss + opts.get((st, pss), 0), st, src, b.state, dst, acc,
+                                                0.0, 0.01, ws))
+            else:
+                C.check(C.cosmos_rk4_stage(b.g, b.p, st, src, b.state, dst, acc, 0.0, 0.01, ws))
+        nx = n[0]
+        assert torch.equal(a.view()[..., :nx], b.view()[..., :nx])
+    # options only where they mean something
+    b = Evolution(C.make_grid(n, h, pitch=pitch), p)
+    U1, acc = torch.empty_like(b.state), torch.empty_like(b.state)
+    for pss, st in ((0 + 16, 2), (2 + 16, 2), (1 + 32, 2), (2 + 32, 4), (2 + 128, 1)):
+        assert C.cosmos_stage_pass(b.g, b.p, pss, st, b.state, b.state, U1, acc, 0.0, 0.01,
+                                   b.ws_rhs) == C.COSMOS_EINVAL
 
 
 def test_gauge_wave_32_cube_20_steps(C, O):
