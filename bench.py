@@ -43,16 +43,16 @@ COMBINE_FLOPS = [2, 4, 4, 3]
 # the algebra pass: the mean over a step's stages 1, 2, 3, 4), and the hash of
 # the kernel sources it was taken on.  Reported scaled to the bench grid by
 # points; null when the kernel sources differ from the profiled ones.
-NCU_TRAFFIC = {"sources_sha256_16": "7d00e3712337ce07", "grid": 96,
+NCU_TRAFFIC = {"sources_sha256_16": "dff190097f86b828", "grid": 96,
                "bytes_per_launch": {
-                   # exponent scan + limb copy + integer pass, mean over the 4 stages of one step
-                   "derivative": ((169877760 + 3154432) + (169883392 + 122640640) + (239138304 + 1097457664)
-                                  + (169892352 + 670976) + (169883136 + 122384384) + (239033344 + 1097472512)
-                                  + (169890816 + 505856) + (169883904 + 121901056) + (239054848 + 1097503488)
-                                  + (169887232 + 370688) + (169884416 + 122266112) + (239174656 + 1097424384)) / 4,
+                   # exponent scan (stage 1 only) + limb copy + integer pass, mean over the 4 stages of a step
+                   "derivative": ((169876736 + 3307776) + (169887232 + 122644992) + (238298368 + 1094820864)
+                                  + (169884672 + 122289152) + (238306816 + 1094944000)
+                                  + (169883392 + 121859072) + (238254336 + 1094992384)
+                                  + (169884160 + 122552832) + (238277888 + 1095010816)) / 4,
                    # algebra pass, modes 1, 2, 2, 3 of one step
-                   "algebra": ((1377011968 + 797183744) + (1683907328 + 697591296) + (1685144832 + 698324224)
-                               + (1673146368 + 477074432)) / 4}}
+                   "algebra": ((1372211968 + 447251712) + (1668633344 + 396210688) + (1669779200 + 395640576)
+                               + (1673173504 + 477020416)) / 4}}
 # derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
 DERIV_DOUBLES = 162
 KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_int.cuh", "limbs.cu", "stage_vac.cu",

@@ -47,7 +47,8 @@ static long max_tiles(const cosmos_grid& g) {
 
 struct BatchLayout {
   std::vector<size_t> A, B, acc, prim, flux, D, limbs;  // per instance, in doubles from ws
-  size_t args, tiles, dtiles, kref, expo;               // byte offsets (expo: n x nslot exponents)
+  size_t args, tiles, dtiles, kref, expo, erec;         // byte offsets (expo: n x nslot exponents; erec:
+                                                        // the algebra passes' record, 32 unsigned per slot)
   size_t total;
 };
 
@@ -86,6 +87,7 @@ static BatchLayout batch_layout(int n, const cosmos_grid* grids, const cosmos_pa
   L.dtiles = take(sizeof(BatchTile) * (size_t)dtiles);
   L.kref = take(sizeof(double) * (size_t)max_steps * 4 * n);
   L.expo = take(sizeof(int) * (size_t)n * nslot_of(p));
+  L.erec = take(sizeof(unsigned) * 32 * (size_t)n * nslot_of(p));  // per instance and slot, one line each
   L.total = off;
   return L;
 }
@@ -229,6 +231,8 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
       a.D = wsd + L.D[i];
       a.L = (const long long*)(wsd + L.limbs[i]);
       a.E = (const int*)(b->ws + L.expo) + (size_t)i * nslot_of(p);
+      // stages 1-3 record the exponents of the state they write for the next stage
+      if (s < 3) a.E_rec = (unsigned*)(b->ws + L.erec) + 32 * (size_t)i * nslot_of(p);
       if (p->fluid) {
         a.prim = wsd + L.prim[i];
         a.flux = wsd + L.flux[i];
@@ -247,7 +251,8 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
         kref[((size_t)st * 4 + s) * n + i] = K_ref(p, ts);
       }
   if (cudaMemcpy(b->d_args, args.data(), sizeof(StageArgs) * args.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_kref, kref.data(), sizeof(double) * kref.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(b->d_kref, kref.data(), sizeof(double) * kref.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->ws + L.erec, 0, sizeof(unsigned) * 32 * (size_t)n * nslot_of(p)) != cudaSuccess) {
     delete b;
     return COSMOS_ECUDA;
   }
@@ -311,9 +316,18 @@ static int batch_launch_steps(cosmos_batch b, int first_step, int steps, cudaStr
           launch_batch_fluid(args, b->d_tiles, b->ntiles, b->tune.mapping, b->p.w, grid, block, s) != cudaSuccess)
         return COSMOS_ECUDA;
       const double* kref = b->d_kref + ((size_t)st * 4 + stage) * b->n;
-      if (launch_batch_limbs(args, b->n, nslot_of(&b->p), b->p.fluid, (int*)(b->ws + b->L.expo), s) != cudaSuccess ||
+      const int ns = nslot_of(&b->p);
+      // stage 1 scans every instance's state; stages 2-4 take the exponents the previous
+      // stage's algebra pass recorded
+      const cudaError_t le = stage == 0
+                                 ? launch_batch_limbs(args, b->n, ns, b->p.fluid, (int*)(b->ws + b->L.expo), s)
+                                 : launch_batch_to_limbs(args, b->n, ns, b->p.fluid, s);
+      if (le != cudaSuccess ||
           launch(args, b->d_tiles, b->ntiles, b->tune.mapping, kref, modes[stage], grid, block, s, b->d_dtiles,
                  b->ndtiles, ideriv_blocks(b), ideriv_near(b)) != cudaSuccess)
+        return COSMOS_ECUDA;
+      if (stage < 3 && launch_exponents_from_record((unsigned*)(b->ws + b->L.erec), (int*)(b->ws + b->L.expo),
+                                                    b->n * ns, s) != cudaSuccess)
         return COSMOS_ECUDA;
     }
   return COSMOS_OK;
@@ -364,7 +378,9 @@ int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stre
     if (rc == COSMOS_OK &&
         (launch_batch_limbs(b->d_args, b->n, nslot_of(&b->p), b->p.fluid, (int*)(b->ws + b->L.expo), s) != cudaSuccess ||
          launch(b->d_args, b->d_tiles, b->ntiles, b->tune.mapping, b->d_kref, MODE_S1, grid, block, s, b->d_dtiles,
-                b->ndtiles, ideriv_blocks(b), ideriv_near(b)) != cudaSuccess))
+                b->ndtiles, ideriv_blocks(b), ideriv_near(b)) != cudaSuccess ||
+         launch_exponents_from_record((unsigned*)(b->ws + b->L.erec), (int*)(b->ws + b->L.expo),
+                                      b->n * nslot_of(&b->p), s) != cudaSuccess))  // leaves the record cleared
       rc = COSMOS_ECUDA;
   }
   cudaEventRecord(e1, s);

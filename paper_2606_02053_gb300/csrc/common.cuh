@@ -171,6 +171,8 @@ cudaError_t launch_field_exponents(const DevGrid& g, const double* U, int fluid,
                                    cudaStream_t s);
 // E[s] = rec[32 s] and rec[32 s] = 0 for s < nslot (the exponents an algebra pass recorded)
 cudaError_t launch_exponents_from_record(unsigned* rec, int* E, int nslot, cudaStream_t s);
+// the batched limb copy with the exponents already in args[i].E
+cudaError_t launch_batch_to_limbs(const StageArgs* args, int n, int nslot, int fluid, cudaStream_t s);
 // the same for every instance of a batch (args[i] = instance i's stage arguments;
 // E_all = the n x nslot exponents, contiguous, args[i].E = E_all + i nslot)
 cudaError_t launch_batch_limbs(const StageArgs* args, int n, int nslot, int fluid, int* E_all, cudaStream_t s);

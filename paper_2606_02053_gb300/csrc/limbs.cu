@@ -133,15 +133,21 @@ cudaError_t launch_field_exponents(const DevGrid& g, const double* U, int fluid,
 }
 
 __global__ void exponents_from_record_kernel(unsigned* __restrict__ rec, int* __restrict__ E, int nslot) {
-  const int s = threadIdx.x;
-  if (s < nslot) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslot; s += gridDim.x * blockDim.x) {
     E[s] = (int)rec[32 * s];
     rec[32 * s] = 0u;
   }
 }
 
 cudaError_t launch_exponents_from_record(unsigned* rec, int* E, int nslot, cudaStream_t s) {
-  exponents_from_record_kernel<<<1, 32, 0, s>>>(rec, E, nslot);
+  exponents_from_record_kernel<<<(nslot + 255) / 256, 256, 0, s>>>(rec, E, nslot);
+  return cudaGetLastError();
+}
+
+// The batched limb copy with the exponents already in args[i].E (no scan).
+cudaError_t launch_batch_to_limbs(const StageArgs* args, int n, int nslot, int fluid, cudaStream_t s) {
+  const dim3 grid(32, (unsigned)nslot, (unsigned)n);
+  batch_to_limbs_kernel<<<grid, 128, 0, s>>>(args, fluid);
   return cudaGetLastError();
 }
 
