@@ -17,7 +17,9 @@ segment's time levels and their RK4 stage states (cosmos_rk4_step_stages), and
 runs cosmos_adjoint_step_stages backwards through them,
 injecting the diagnostics' cotangents at the step they were measured, then
 cosmos_init_zeta_vjp.  zeta = mu * profile built with torch gives d/d mu by
-ordinary autograd.
+ordinary autograd.  ``CollapseRun.backward_many`` gives the zeta gradients of
+several cotangent pairs (e.g. each diagnostic on its own) in one reverse sweep
+that replays each checkpoint segment once for all of them.
 """
 from __future__ import annotations
 
@@ -88,11 +90,20 @@ class CollapseRun:
 
     def backward(self, rec, gbar_alpha, gbar_comp):
         """zeta_bar for the cotangents of (min lapse, peak compaction)."""
-        lam = self.new_state()
-        C.check(C.cosmos_compaction_vjp(self.g, self.p, rec["final"], rec["kstar"], self.kmax, rec["aux"],
-                                        float(gbar_comp), lam))
-        if rec["nstar"] == self.steps:
-            C.check(C.cosmos_central_lapse_vjp(self.g, self.p, gbar_alpha, lam))
+        return self.backward_many(rec, [(gbar_alpha, gbar_comp)])[0]
+
+    def backward_many(self, rec, seeds):
+        """zeta_bar for each pair (gbar_alpha, gbar_comp) in `seeds`, in one reverse sweep:
+        every checkpoint segment is replayed forward once, and each step's adjoint runs
+        for every pair on the same replayed stage states."""
+        lams = []
+        for ga, gc in seeds:
+            lam = self.new_state()
+            C.check(C.cosmos_compaction_vjp(self.g, self.p, rec["final"], rec["kstar"], self.kmax, rec["aux"],
+                                            float(gc), lam))
+            if rec["nstar"] == self.steps:
+                C.check(C.cosmos_central_lapse_vjp(self.g, self.p, float(ga), lam))
+            lams.append(lam)
         starts = sorted(rec["checkpoints"].keys())
         for si in reversed(range(len(starts))):
             s0 = starts[si]
@@ -106,14 +117,18 @@ class CollapseRun:
                 C.check(C.cosmos_rk4_step_stages(self.g, self.p, U, s * self.dt, self.dt, *stages, self.ws_rk4))
             for s in reversed(range(s0, s1)):
                 Un, (U2, U3, U4) = saved[s - s0]
-                C.check(C.cosmos_adjoint_step_stages(self.g, self.p, Un, U2, U3, U4, lam, lam, s * self.dt, self.dt,
-                                                     self.ws_adj))
-                if s == rec["nstar"]:
-                    C.check(C.cosmos_central_lapse_vjp(self.g, self.p, gbar_alpha, lam))
+                for lam, (ga, _) in zip(lams, seeds):
+                    C.check(C.cosmos_adjoint_step_stages(self.g, self.p, Un, U2, U3, U4, lam, lam, s * self.dt,
+                                                         self.dt, self.ws_adj))
+                    if s == rec["nstar"]:
+                        C.check(C.cosmos_central_lapse_vjp(self.g, self.p, float(ga), lam))
             del saved
-        zbar = torch.empty(self.fs, dtype=torch.float64, device=self.device)
-        C.check(C.cosmos_init_zeta_vjp(self.g, self.p, rec["U0"], lam, zbar, self.ws_ivjp))
-        return zbar
+        zbars = []
+        for lam in lams:
+            zbar = torch.empty(self.fs, dtype=torch.float64, device=self.device)
+            C.check(C.cosmos_init_zeta_vjp(self.g, self.p, rec["U0"], lam, zbar, self.ws_ivjp))
+            zbars.append(zbar)
+        return zbars
 
 
 class CosmosAdjoint(torch.autograd.Function):

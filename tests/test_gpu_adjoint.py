@@ -321,3 +321,21 @@ def test_collapse_gradients_from_a_fluid_at_rest_match_the_oracle_tape(C, O):
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     zeta = 0.6 * np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * 0.15 ** 2))
     collapse_case(C, O, n, 4, 2, zeta)
+
+
+def test_one_sweep_for_both_diagnostics_equals_two(C):
+    """backward_many replays each checkpoint segment once for several cotangent pairs;
+    each zeta_bar is bitwise the one a separate sweep gives."""
+    from paper_2606_02053_gb300.adjoint import CollapseRun
+
+    n = 12
+    h = 1.0 / n
+    run = CollapseRun(n, C.make_params(fluid=1, w=1.0 / 3.0, H0=20.0), dt=0.25 * h, steps=7, checkpoint_every=3)
+    x = (-(n // 2) + torch.arange(n, dtype=torch.float64, device="cuda")) * h
+    Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+    zeta = (0.6 * torch.exp(-((X - 0.01) ** 2 + Y ** 2 + Z ** 2) / (2 * 0.15 ** 2))).reshape(-1).contiguous()
+    _, _, rec = run.forward(zeta)
+    pairs = [(1.0, 0.0), (0.0, 1.0), (0.3, -2.0)]
+    many = run.backward_many(rec, pairs)
+    for (ga, gc), zb in zip(pairs, many):
+        assert torch.equal(zb, run.backward(rec, ga, gc))
