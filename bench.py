@@ -6,9 +6,15 @@ Gamma-driver shift, amplitude 0.01, wavelength = box, dt = h/4.
 One step = one full RK4 step (4 fused stage launches) over the whole grid.
 The state (3.2 GB) is larger than L2 (129 MB), so every step streams from HBM.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+The same line carries the rest of the metric, measured on one GPU: the same
+sweep on a generic state (sweep_generic), the 64-instance batched scan against
+the per-instance loop (batched) and the 96^3 adjoint against finite
+differences (adjoint).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--decompose]
 Prints one JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
-rank evolves its own 256^3 instance (independent replicas, weak scaling).
+rank evolves its own 256^3 instance (independent replicas, weak scaling); with
+--decompose the ranks hold z-slabs of one 256^3 grid (strong scaling).
 """
 from __future__ import annotations
 
