@@ -664,17 +664,27 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
             (e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s, 2, fb[c], fb[c + 1])))
           return e;
       }
-      if ((e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s, 5))) return e;
-    } else if ((e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s))) {
+      if ((e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s, 5, 0, 0, 0, 0, nullptr,
+                         6)))
+        return e;
+    } else if ((e = run_stage(g, p, MODE_S1, dev_state, dev_state, A, acc, ts, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0,
+                              nullptr, 6))) {
       return e;
     }
-    if ((e = run_stage(g, p, MODE_S23, A, dev_state, B, acc, ts + dt2, dt2, 2.0, w, L, s))) return e;
-    if ((e = run_stage(g, p, MODE_S23, B, dev_state, A, acc, ts + dt2, dt, 2.0, w, L, s))) return e;
+    // as cosmos_rk4_step: stages 2-4 take the exponents the algebra pass before recorded
+    if ((e = run_stage(g, p, MODE_S23, A, dev_state, B, acc, ts + dt2, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
+      return e;
+    if ((e = run_stage(g, p, MODE_S23, B, dev_state, A, acc, ts + dt2, dt, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
+      return e;
     if (step + 1 < steps) {
-      if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s))) return e;
+      if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s, 7, 0, 0, 0, 0,
+                         nullptr, 1)))
+        return e;
       continue;
     }
-    if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s, 3))) return e;
+    if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s, 3, 0, 0, 0, 0,
+                       nullptr, 1)))
+      return e;
     for (int sl = 0; sl < nsl; ++sl) {
       const int k0 = sl * g->nz / nsl, k1 = (sl + 1) * g->nz / nsl;
       if ((e = run_stage(g, p, MODE_S4, A, dev_state, nullptr, acc, ts + dt, dt / 6.0, 2.0, w, L, s, 4, 0, 0, k0,
