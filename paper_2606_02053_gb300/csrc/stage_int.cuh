@@ -85,22 +85,19 @@ __device__ __forceinline__ double round_mag(unsigned long long uh, unsigned long
   return __longlong_as_double((long long)bits);
 }
 
-// round_mag for a magnitude below 2^63 (uh = 0), bitwise the same: round to
-// nearest even by adding half a unit of the last kept place less one plus the
-// kept part's lowest bit and truncating (no overflow: lo < 2^63); the leading
-// one, or a carry out of the significand, adds into the exponent field.
+// round_mag for a magnitude below 2^63 (uh = 0), bitwise the same, without a
+// branch on the magnitude (the lanes of a warp hold sums of every size): the
+// leading one is moved to bit 62 (exact, lo < 2^63), then the low 10 bits are
+// dropped with round to nearest even by adding 0x1FF plus the lowest kept bit
+// (no overflow: x < 2^63).  Sums of at most 53 significant bits have those 10
+// bits zero and pass unchanged.  The leading one, or a carry out of the
+// significand, adds into the exponent field.
 __device__ __forceinline__ double round_mag64(unsigned long long lo, bool neg, int e_ref) {
   if (lo == 0) return 0.0;
-  const int n = 63 - __clzll(lo);
-  const int ex = n + e_ref - 1085 + 1023;  // biased exponent of the leading one
-  unsigned long long m;
-  if (n <= 52) {
-    m = lo << (52 - n);
-  } else {
-    const int r = n - 52;
-    m = (lo + ((1ull << (r - 1)) - 1ull) + ((lo >> r) & 1ull)) >> r;
-  }
-  const long long b = ((long long)(ex - 1) << 52) + (long long)m;  // m in [2^52, 2^53]
+  const int n = 63 - __clzll(lo);  // position of the leading one, 0..62
+  const unsigned long long x = lo << (62 - n);
+  const unsigned long long m = (x + 0x1FFull + ((x >> 10) & 1ull)) >> 10;  // in [2^52, 2^53]
+  const long long b = ((long long)(n + e_ref - 63) << 52) + (long long)m;  // biased exponent n + e_ref - 62
   if ((b >> 52) <= 0) return neg ? -0.0 : 0.0;  // below the normal range (as round_mag)
   return __longlong_as_double((long long)((unsigned long long)b | ((unsigned long long)neg << 63)));
 }
