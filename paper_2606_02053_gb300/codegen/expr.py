@@ -340,9 +340,78 @@ def op_counts(g: Graph, outputs: Sequence[Ex]) -> Dict[str, int]:
     return c
 
 
+_SUM_OPS = ("add", "sub", "neg")
+
+
+def sum_chains(g: Graph, order: Sequence[int], out_ids: Sequence[int]):
+    """The sums of the emitted code that are rebuilt as multiply-add chains.
+
+    A sum tree is a maximal set of add / sub / neg nodes in which every node but
+    the root has exactly one user, another node of the tree (and is no output).
+    Its terms are the operands below it with their signs.  The real value is
+    the same in any order of the terms; the rounding is that of a sequential
+    sum.  A tree of k >= 3 terms becomes the chain acc = t_1, acc = acc +- t_j,
+    whose every step can absorb a product term into one DFMA; the chain starts
+    with a term that is not a product when there is one (so that no product is
+    left as a lone multiply), the others follow in the order they become
+    available, which keeps the products short-lived.
+
+    Returns ({root: [(sign, term), ...]}, the set of interior nodes)."""
+    uses: Dict[int, List[int]] = {}
+    for n in order:
+        for a in g.args[n]:
+            uses.setdefault(a, []).append(n)
+    outs = set(out_ids)
+
+    def interior(n):
+        u = uses.get(n, [])
+        return g.ops[n] in _SUM_OPS and len(u) == 1 and n not in outs and g.ops[u[0]] in _SUM_OPS
+
+    pos = {n: i for i, n in enumerate(order)}
+    chains: Dict[int, List[tuple]] = {}
+    inner = set()
+    for n in order:
+        if g.ops[n] not in _SUM_OPS or interior(n):
+            continue
+        terms: List[tuple] = []
+        seen_inner: List[int] = []
+
+        def collect(x, s, top):
+            if top or interior(x):
+                if not top:
+                    seen_inner.append(x)
+                op, a = g.ops[x], g.args[x]
+                if op == "add":
+                    collect(a[0], s, False)
+                    collect(a[1], s, False)
+                elif op == "sub":
+                    collect(a[0], s, False)
+                    collect(a[1], -s, False)
+                else:  # neg
+                    collect(a[0], -s, False)
+            else:
+                terms.append((s, x))
+
+        collect(n, 1, True)
+        if len(terms) < 3:
+            continue
+        by_pos = sorted(terms, key=lambda st: pos[st[1]])
+        lead = [st for st in by_pos if g.ops[st[1]] != "mul"]
+        if lead:
+            pos_lead = [st for st in lead if st[0] > 0]
+            first = (pos_lead or lead)[0]
+        else:
+            first = by_pos[0]
+        rest = list(by_pos)
+        rest.remove(first)
+        chains[n] = [first] + rest
+        inner.update(seen_inner)
+    return chains, inner
+
+
 def emit_function(g: Graph, fname: str, in_names: Sequence[str], out_exprs: Sequence[Ex], params: Sequence[str],
                   in_array="in", out_array="out", param_struct="p", qualifiers="__device__ __forceinline__",
-                  extra_args="", accessors=False, order=None) -> str:
+                  extra_args="", accessors=False, order=None, chains=True) -> str:
     """Emit `void fname(const double* in, double* out, const ParamT& p)`.
 
     in_names[i] is the input name stored at in[i]; outputs go to out[k].
@@ -350,7 +419,9 @@ def emit_function(g: Graph, fname: str, in_names: Sequence[str], out_exprs: Sequ
     types (anything with ``in[i]`` and ``out[k] = v``, e.g. loads straight from
     global memory and a store functor), and each output is written as soon as
     its value exists.  ``order`` (a list of the reachable non-leaf nodes) fixes
-    the statement order; the default is creation (topological) order."""
+    the statement order; the default is creation (topological) order.  With
+    ``chains`` every sum of three or more terms is written as a multiply-add
+    chain (``sum_chains``): each step is emitted as soon as its term exists."""
     in_index = {nm: i for i, nm in enumerate(in_names)}
     reach = _reachable(g, [o.id for o in out_exprs])
     if order is None:
@@ -362,10 +433,25 @@ def emit_function(g: Graph, fname: str, in_names: Sequence[str], out_exprs: Sequ
     outs_of: Dict[int, List[int]] = {}
     for k, o in enumerate(out_exprs):
         outs_of.setdefault(o.id, []).append(k)
+    cmap, inner = sum_chains(g, order, [o.id for o in out_exprs]) if chains else ({}, set())
+    pos = {n: i for i, n in enumerate(order)}
+    steps_at: Dict[int, List[tuple]] = {}  # position -> [(root, step index)]
+    for r, terms in cmap.items():
+        p = -1
+        for j, (_, x) in enumerate(terms):
+            p = max(p, pos[x])
+            steps_at.setdefault(p, []).append((r, j))
     names: Dict[int, str] = {}
     lines = []
     written = set()
-    for n in order:
+
+    def write_outputs(n, t):
+        if accessors:
+            for k in outs_of.get(n, []):
+                lines.append(f"  {out_array}[{k}] = {t};")
+                written.add(k)
+
+    for i, n in enumerate(order):
         op = g.ops[n]
         if op == "in":
             nm = g.data[n]
@@ -376,14 +462,24 @@ def emit_function(g: Graph, fname: str, in_names: Sequence[str], out_exprs: Sequ
             names[n] = f"{param_struct}.{g.data[n]}"
         elif op == "const":
             names[n] = _fmt(g.data[n])
-        else:
+        elif n not in inner and n not in cmap:
             t = f"t{n}"
             lines.append(f"  const double {t} = {_expr(g, n, lambda a: names[a])};")
             names[n] = t
-            if accessors:
-                for k in outs_of.get(n, []):
-                    lines.append(f"  {out_array}[{k}] = {t};")
-                    written.add(k)
+            write_outputs(n, t)
+        for r, j in steps_at.get(i, []):
+            terms = cmap[r]
+            s, x = terms[j]
+            last = j == len(terms) - 1
+            t = f"t{r}" if last else f"t{r}_{j}"
+            if j == 0:
+                rhs = names[x] if s > 0 else f"-{names[x]}"
+            else:
+                rhs = f"t{r}_{j - 1} {'+' if s > 0 else '-'} {names[x]}"
+            lines.append(f"  const double {t} = {rhs};")
+            if last:
+                names[r] = t
+                write_outputs(r, t)
     for k, o in enumerate(out_exprs):
         if k not in written:
             lines.append(f"  {out_array}[{k}] = {names[o.id]};")

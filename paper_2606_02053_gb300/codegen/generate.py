@@ -78,21 +78,26 @@ def render() -> dict:
     g, names, out = fluid_dsl.prim()
     stats.append(("prim", op_counts(g, out)))
     fb.append("// inputs: " + ", ".join(names))
-    fb.append(emit_function(g, "fluid_prim", names, out, ["FluidParams"]))
+    # The fluid header keeps the sums as the formulas group them (no multiply-add chains): a
+    # face flux is symmetric under the exchange of its left and right states (with the odd
+    # components negated), and its paired sums (F_L + F_R, U_R - U_L) keep that symmetry bitwise,
+    # so mirror-symmetric data keep their velocities exactly zero on the symmetry planes.
+    fb.append(emit_function(g, "fluid_prim", names, out, ["FluidParams"], chains=False))
     qb = [g.input(f"qb{m}") for m in range(4)]
     adj = vjp(g, out, qb, [Ex(g, g.inputs[nm]) for nm in names])
     fb.append("// reverse mode: in[11 + m] = cotangent of (rho, v0, v1, v2)[m]; out = cotangents of the inputs")
-    fb.append(emit_function(g, "fluid_prim_vjp", names + [f"qb{m}" for m in range(4)], adj, ["FluidParams"]))
+    fb.append(emit_function(g, "fluid_prim_vjp", names + [f"qb{m}" for m in range(4)], adj, ["FluidParams"],
+                            chains=False))
     for d in range(3):
         g, names, out = fluid_dsl.face_flux(d)
         stats.append((f"face{d}", op_counts(g, out)))
         if d == 0:
             fb.append("// face-flux inputs: " + ", ".join(names))
-        fb.append(emit_function(g, f"fluid_face_flux_{d}", names, out, ["FluidParams"]))
+        fb.append(emit_function(g, f"fluid_face_flux_{d}", names, out, ["FluidParams"], chains=False))
         hb = [g.input(f"hb{m}") for m in range(4)]
         adj = vjp(g, out, hb, [Ex(g, g.inputs[nm]) for nm in names])
         fb.append(emit_function(g, f"fluid_face_flux_{d}_vjp", names + [f"hb{m}" for m in range(4)], adj,
-                                ["FluidParams"]))
+                                ["FluidParams"], chains=False))
     files["fluid_algebra.cuh"] = "\n".join(fb)
     return files, stats
 
