@@ -136,6 +136,10 @@ __device__ __forceinline__ int limb_field(int s, int fluid) { return (fluid && s
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int3 ldl(const long long* __restrict__ L, int o) { return digits(__ldg(L + o)); }
 
+// Digit sums staged in shared memory as int4 (w unused): one 128-bit access each.
+__device__ __forceinline__ int4 p4(int3 v) { return make_int4(v.x, v.y, v.z, 0); }
+__device__ __forceinline__ int3 q3(int4 v) { return make_int3(v.x, v.y, v.z); }
+
 // Periodic neighbour offsets of one point within one field, as 32-bit
 // element offsets (a field of the grids this pass accepts has < 2^31 points).
 struct NbrI {
@@ -181,21 +185,21 @@ __device__ __forceinline__ int limb_plane_off(const DevGrid& g, int x, int y, in
 // the x-extended tile (halo 2), unscaled.
 template <bool NEAR>
 __device__ __forceinline__ void stage_dydz_int(const DevGrid& g, const long long* __restrict__ Lf, int i0, int j0,
-                                                 int k, int tid, int3* __restrict__ sDy, int3* __restrict__ sDz) {
+                                                 int k, int tid, int4* __restrict__ sDy, int4* __restrict__ sDz) {
   constexpr int TXH = BX + 4;
   for (int q = tid; q < TXH * DBY; q += BX * DBY) {
     const int qx = q % TXH, qy = q / TXH;
     const int x = i0 - 2 + qx, y = j0 + qy;
-    sDy[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y + 1, k)),
-                               ldl(Lf, limb_plane_off<NEAR>(g, x, y - 1, k))), 8),
-                   l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y + 2, k)), ldl(Lf, limb_plane_off<NEAR>(g, x, y - 2, k))));
+    sDy[q] = p4(l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y + 1, k)),
+                                  ldl(Lf, limb_plane_off<NEAR>(g, x, y - 1, k))), 8),
+                      l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y + 2, k)), ldl(Lf, limb_plane_off<NEAR>(g, x, y - 2, k)))));
   }
   for (int q = tid; q < TXH * (DBY + 4); q += BX * DBY) {
     const int qx = q % TXH, qy = q / TXH;
     const int x = i0 - 2 + qx, y = j0 - 2 + qy;
-    sDz[q] = l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y, k + 1)),
-                               ldl(Lf, limb_plane_off<NEAR>(g, x, y, k - 1))), 8),
-                   l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y, k + 2)), ldl(Lf, limb_plane_off<NEAR>(g, x, y, k - 2))));
+    sDz[q] = p4(l_sub(l_mul(l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y, k + 1)),
+                                  ldl(Lf, limb_plane_off<NEAR>(g, x, y, k - 1))), 8),
+                      l_sub(ldl(Lf, limb_plane_off<NEAR>(g, x, y, k + 2)), ldl(Lf, limb_plane_off<NEAR>(g, x, y, k - 2)))));
   }
 }
 
@@ -252,8 +256,8 @@ __device__ __forceinline__ void ideriv_d1_point(const StageArgs& a, int m, const
 // formed; D_y and D_z sums come from the staging area.
 template <class T>
 __device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, const NbrI& n, int tx, int ty,
-                                                bool ko_equal, const int3* __restrict__ sDy,
-                                                const int3* __restrict__ sDz) {
+                                                bool ko_equal, const int4* __restrict__ sDy,
+                                                const int4* __restrict__ sDz) {
   constexpr int TXH = BX + 4;
   const long fs = a.g.fstride;
   const Coef& c = a.c;
@@ -289,21 +293,23 @@ __device__ __forceinline__ void ideriv_d2_point(const StageArgs& a, int m2, cons
     if (ko_equal) ko = from_limbs(l_mad(f0, -60, l_mad(P2, -6, l_mad(P1, 15, P3))), e);  // scaled in the algebra pass
     D[(long)(NDER0 + s) * fs + n.c] = ko;
   }
-  const int3* ry = sDy + ty * TXH + tx + 2;        // D_y sums at (i + o, j)
-  const int3* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z sums at (i + o, j), row stride TXH along y
-  D[(long)(3 * m1 + 1) * fs + n.c] = from_limbs(ry[0], e) * c.d1b[1];
-  D[(long)(3 * m1 + 2) * fs + n.c] = from_limbs(rz[0], e) * c.d1b[2];
-  D[b + 1 * fs] = from_limbs(l_sub(l_mul(l_sub(ry[1], ry[-1]), 8), l_sub(ry[2], ry[-2])), e) * c.mix[0];
-  D[b + 2 * fs] = from_limbs(l_sub(l_mul(l_sub(rz[1], rz[-1]), 8), l_sub(rz[2], rz[-2])), e) * c.mix[1];
-  D[b + 4 * fs] =
-      from_limbs(l_sub(l_mul(l_sub(rz[TXH], rz[-TXH]), 8), l_sub(rz[2 * TXH], rz[-2 * TXH])), e) * c.mix[2];
+  const int4* ry = sDy + ty * TXH + tx + 2;        // D_y sums at (i + o, j)
+  const int4* rz = sDz + (ty + 2) * TXH + tx + 2;  // D_z sums at (i + o, j), row stride TXH along y
+  D[(long)(3 * m1 + 1) * fs + n.c] = from_limbs(q3(ry[0]), e) * c.d1b[1];
+  D[(long)(3 * m1 + 2) * fs + n.c] = from_limbs(q3(rz[0]), e) * c.d1b[2];
+  D[b + 1 * fs] =
+      from_limbs(l_sub(l_mul(l_sub(q3(ry[1]), q3(ry[-1])), 8), l_sub(q3(ry[2]), q3(ry[-2]))), e) * c.mix[0];
+  D[b + 2 * fs] =
+      from_limbs(l_sub(l_mul(l_sub(q3(rz[1]), q3(rz[-1])), 8), l_sub(q3(rz[2]), q3(rz[-2]))), e) * c.mix[1];
+  D[b + 4 * fs] = from_limbs(l_sub(l_mul(l_sub(q3(rz[TXH]), q3(rz[-TXH])), 8),
+                                   l_sub(q3(rz[2 * TXH]), q3(rz[-2 * TXH]))), e) * c.mix[2];
 }
 
 // One BX x DBY tile of one z-plane (block of BX x DBY threads); the D_y / D_z
 // sums of one second-derivative field at a time are staged in shared memory.
 template <class T, bool NEAR>
-__device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, int k, int3* __restrict__ sDy,
-                                            int3* __restrict__ sDz) {
+__device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, int k, int4* __restrict__ sDy,
+                                            int4* __restrict__ sDz) {
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int i = i0 + tx, j = j0 + ty;
   const bool valid = i < a.g.nx && j < a.g.ny;
@@ -331,7 +337,7 @@ __device__ __forceinline__ void ideriv_tile(const StageArgs& a, int i0, int j0, 
 // NEAR: near_indices holds for the grid (for every grid of a batch).
 template <class T, bool NEAR>
 __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS) ideriv_kernel(const StageArgs a) {
-  __shared__ int3 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
+  __shared__ int4 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
   ideriv_tile<T, NEAR>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
 }
 
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS) ideriv_kern
 template <class T, bool NEAR>
 __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS)
     batch_ideriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
-  __shared__ int3 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
+  __shared__ int4 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
   for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
     const BatchTile t = tiles[w];
     ideriv_tile<T, NEAR>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);

@@ -10,6 +10,8 @@ one and by properties that hold at any size:
   differences vanish exactly on both sides) and every (y, z) row must match it;
 * one right-hand side of a generic smooth state at 256^3, sampled at interior,
   face, edge and corner points against the oracle's per-point right-hand side;
+* the same on a 250 x 198 x 203 grid (ragged derivative tiles in x and y, no
+  axis a multiple of the tile), sampled at the tile edges and the periodic faces;
 * 128^3 radiation FLRW + Gaussian zeta (mu = 0.5, sigma = L/8, H0 L = 40),
   200 RK4 steps: constraint norms reported, the symmetry of the data under
   axis permutations and reflections kept to rounding, and the right-hand side
@@ -103,6 +105,30 @@ def test_rhs_sampled_parity_generic_state_256(C, O):
     torch.cuda.empty_cache()
     pts = sample_points(n, 1500, seed=17)
     ref = O.rhs_points(O.OGrid((n, n, n), h), oracle_params(O, p), s, pts, 0.0)
+    err = sampled_rhs_errors(r, ref, pts)
+    assert err.max() <= RHS_TOL, (err.argmax(), err.max())
+
+
+def test_rhs_sampled_parity_ragged_large_grid(C, O):
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    n = (250, 198, 203)
+    h = 1.0 / 256
+    p = C.make_params(slicing=0, shift=1, eta=2.0, ko_sigma=0.1)
+    s = inputs.smooth_state(n, seed=2562, kmax=4, scale=0.5)
+    ev = Evolution(C.make_grid(n, h), p)
+    ev.set_state(s)
+    r = ev.get(ev.rhs(0.0))
+    del ev
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(19)
+    pts = [[rng.integers(0, m) for m in n] for _ in range(800)]
+    xs, ys = [0, 1, 2, 31, 32, 245, 247, 249], [0, 2, 7, 8, 100, 191, 192, 197]
+    ks = [0, 1, 2, 3, 7, 8, 9, 15, 16, 100, 191, 192, 199, 200, 201, 202]
+    pts += [[x, y, k] for x in xs for y in ys for k in ks]
+    pts = np.unique(np.array(pts, dtype=np.int64), axis=0)
+    ref = O.rhs_points(O.OGrid(n, h), oracle_params(O, p), s, pts, 0.0)
     err = sampled_rhs_errors(r, ref, pts)
     assert err.max() <= RHS_TOL, (err.argmax(), err.max())
 
