@@ -49,16 +49,16 @@ COMBINE_FLOPS = [2, 4, 4, 3]
 # the algebra pass: the mean over a step's stages 1, 2, 3, 4), and the hash of
 # the kernel sources it was taken on.  Reported scaled to the bench grid by
 # points; null when the kernel sources differ from the profiled ones.
-NCU_TRAFFIC = {"sources_sha256_16": "dff190097f86b828", "grid": 96,
+NCU_TRAFFIC = {"sources_sha256_16": "8db15fd6f6a7d713", "grid": 96,
                "bytes_per_launch": {
                    # exponent scan (stage 1 only) + limb copy + integer pass, mean over the 4 stages of a step
-                   "derivative": ((169876736 + 3307776) + (169887232 + 122644992) + (238298368 + 1094820864)
-                                  + (169884672 + 122289152) + (238306816 + 1094944000)
-                                  + (169883392 + 121859072) + (238254336 + 1094992384)
-                                  + (169884160 + 122552832) + (238277888 + 1095010816)) / 4,
+                   "derivative": ((169878016 + 3215872) + (169889792 + 122542080) + (237255680 + 1092109056)
+                                  + (169890304 + 122353152) + (237198080 + 1092582400)
+                                  + (169882624 + 121916160) + (237166592 + 1092224000)
+                                  + (169893120 + 122293504) + (237318656 + 1092241152)) / 4,
                    # algebra pass, modes 1, 2, 2, 3 of one step
-                   "algebra": ((1372211968 + 447251712) + (1668633344 + 396210688) + (1669779200 + 395640576)
-                               + (1673173504 + 477020416)) / 4}}
+                   "algebra": ((1382648576 + 493276672) + (1673435136 + 457987840) + (1675968256 + 458668544)
+                               + (1659180288 + 432637952)) / 4}}
 # derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
 DERIV_DOUBLES = 162
 KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_int.cuh", "limbs.cu", "stage_vac.cu",
