@@ -257,16 +257,18 @@ int cosmos_batch_plan(int n, const cosmos_grid* grids, const cosmos_params* p, c
     return COSMOS_ECUDA;
   }
   {
+    // Derivative-pass tiles instance by instance, plane by plane: the resident
+    // blocks of the persistent pass then work on neighbouring planes of one grid,
+    // whose z-stencils share their planes in L2 (interleaving the instances, as
+    // for the pointwise passes, spread them over every grid at once and sent the
+    // shared planes back to DRAM).
     std::vector<BatchTile> dt;
-    long most = 0;
-    for (int i = 0; i < n; ++i) most = std::max(most, deriv_tiles(grids[i]));
-    for (long w = 0; w < most; ++w)
-      for (int i = 0; i < n; ++i) {
-        const cosmos_grid& g = grids[i];
-        if (w >= deriv_tiles(g)) continue;
-        const int tx = (g.nx + BX - 1) / BX, ty = (g.ny + DBY - 1) / DBY;
+    for (int i = 0; i < n; ++i) {
+      const cosmos_grid& g = grids[i];
+      const int tx = (g.nx + BX - 1) / BX, ty = (g.ny + DBY - 1) / DBY;
+      for (long w = 0; w < deriv_tiles(g); ++w)
         dt.push_back(BatchTile{i, (int)(w % tx), (int)((w / tx) % ty), (int)(w / ((long)tx * ty))});
-      }
+    }
     b->ndtiles = (long)dt.size();
     if (cudaMemcpy(b->d_dtiles, dt.data(), sizeof(BatchTile) * dt.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
       delete b;

@@ -341,14 +341,30 @@ __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS) ideriv_kern
   ideriv_tile<T, NEAR>(a, blockIdx.x * BX, blockIdx.y * DBY, blockIdx.z, sDy, sDz);
 }
 
-// Persistent batched integer derivative pass over BX x DBY tiles of every instance.
+// Persistent batched integer derivative pass over BX x DBY tiles of every
+// instance.  Each tile's instance arguments are copied to shared memory first:
+// read from there they cannot alias the derivative stores, so they need not
+// be reloaded from global memory after each store.
 template <class T, bool NEAR>
 __global__ void __launch_bounds__(BX* DBY, COSMOS_IDERIV_MIN_BLOCKS)
     batch_ideriv_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles) {
   __shared__ int4 sDy[(BX + 4) * DBY], sDz[(BX + 4) * (DBY + 4)];
+  __shared__ StageArgs sa;
+  static_assert(sizeof(StageArgs) % sizeof(long long) == 0, "StageArgs is copied in 8-byte words");
+  constexpr int W = (int)(sizeof(StageArgs) / sizeof(long long));
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  int inst = -1;
   for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
     const BatchTile t = tiles[w];
-    ideriv_tile<T, NEAR>(args[t.inst], t.a * BX, t.b * DBY, t.c, sDy, sDz);
+    if (t.inst != inst) {  // uniform across the block
+      __syncthreads();     // every thread is done with the previous instance's arguments
+      const long long* src = reinterpret_cast<const long long*>(args + t.inst);
+      long long* dst = reinterpret_cast<long long*>(&sa);
+      for (int q = tid; q < W; q += BX * DBY) dst[q] = src[q];
+      __syncthreads();
+      inst = t.inst;
+    }
+    ideriv_tile<T, NEAR>(sa, t.a * BX, t.b * DBY, t.c, sDy, sDz);
   }
 }
 
