@@ -297,17 +297,31 @@ __device__ __forceinline__ bool batch_point(const BatchTile& t, const DevGrid& g
 
 // Persistent batched algebra pass: blocks stride over the flat work list of
 // all instances; instance `inst` uses args[inst] with K_ref taken from kref.
+// The instance's arguments are copied to shared memory when the instance
+// changes: read from there they cannot alias the pass's stores.
 template <class T, int MODE>
 __global__ void __launch_bounds__(BX* BY, COSMOS_STAGE_MIN_BLOCKS)
     batch_stage_kernel(const StageArgs* __restrict__ args, const BatchTile* __restrict__ tiles, long ntiles,
                        int mapping, const double* __restrict__ kref) {
+  __shared__ StageArgs sa;
+  static_assert(sizeof(StageArgs) % sizeof(long long) == 0, "StageArgs is copied in 8-byte words");
+  constexpr int W = (int)(sizeof(StageArgs) / sizeof(long long));
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+  int inst = -1;
   for (long w = blockIdx.x; w < ntiles; w += gridDim.x) {
     const BatchTile t = tiles[w];
-    const StageArgs& a = args[t.inst];
-    AlgebraParams ap = a.ap;
+    if (t.inst != inst) {  // uniform across the block
+      __syncthreads();     // every thread is done with the previous instance's arguments
+      const long long* src = reinterpret_cast<const long long*>(args + t.inst);
+      long long* dst = reinterpret_cast<long long*>(&sa);
+      for (int q = tid; q < W; q += nthr) dst[q] = src[q];
+      __syncthreads();
+      inst = t.inst;
+    }
+    AlgebraParams ap = sa.ap;
     ap.Kref = kref[t.inst];
     int i, j, k;
-    if (batch_point(t, a.g, mapping, i, j, k)) alg_point<T, MODE>(a, ap, i, j, k);
+    if (batch_point(t, sa.g, mapping, i, j, k)) alg_point<T, MODE>(sa, ap, i, j, k);
   }
 }
 
