@@ -515,7 +515,8 @@ int cosmos_fmr_restrict(const cosmos_fmr* m, const cosmos_params* p, int level, 
  * launched (e.g. 256^3 vacuum fits; with the fluid on, up to about 80^3).
  * The first call made with a device current resolves the array's device
  * address for that device (cudaGetSymbolAddress) and keeps it for the rest
- * of the process; make that first call before any stream capture.  After a
+ * of the process.  The call cannot run under stream capture: it copies the
+ * norms to the host and synchronises `stream`.  After a
  * cudaDeviceReset the kept address may no longer be valid: this call is not
  * for processes that reset a device they have used it on.  The call
  * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
