@@ -265,6 +265,30 @@ int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double*
 int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
                        double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
+/* End-to-end steps of `count` independent states with HOST buffers, pipelined
+ * (the paper's evolution applied to a sequence of grids, e.g. the states of a
+ * parameter scan kept in host memory): state i is copied from host_in[i] to
+ * a device buffer, advanced `steps` RK4 steps from time t, and copied back to
+ * host_out[i]; every result is bitwise that of cosmos_rk4_step applied
+ * `steps` times (and of cosmos_evolve_host).  State i lives in
+ * dev_states[i % nbuf] (nbuf caller-owned device buffers of
+ * cosmos_field_stride * nfields doubles, 1 <= nbuf <= 16, not overlapping).
+ * The copy to the device runs on one private stream, the copy back on
+ * another, and the states are advanced in order on `stream`: with pinned
+ * host buffers and nbuf >= 2 the copies of the other states overlap each
+ * state's computation and each other (pageable buffers give the same
+ * results without the overlap).  host_in[i] may repeat (the same inputs
+ * evolved again); no host_out[i] may overlap any host_in[j] (COSMOS_EINVAL);
+ * host_out entries may repeat (the later state's result is left there).
+ * ws: COSMOS_OP_RK4 bytes (unused when steps = 0).  Synchronous: returns when
+ * every result is in host memory.  Errors: COSMOS_EINVAL (count or steps < 0,
+ * nbuf out of range, a NULL or overlapping buffer), COSMOS_EALIGN,
+ * COSMOS_EWORKSPACE, COSMOS_ECUDA (then the contents of the buffers are
+ * undefined). */
+int cosmos_evolve_host_many(const cosmos_grid* g, const cosmos_params* p, int count, const double* const* host_in,
+                            double* const* host_out, double* const* dev_states, int nbuf, int steps, double t,
+                            double dt, void* ws, size_t ws_bytes, void* stream);
+
 /* Hamiltonian and (conformal) momentum constraints, the parts of the
  * Einstein equations that the initial data must satisfy (section "Physical
  * system settings", initial-data paragraph: the fluid is generated to meet

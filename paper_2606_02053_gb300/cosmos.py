@@ -88,6 +88,8 @@ _SIGS = {
                                _P], ctypes.c_int),
     "cosmos_stage_pass": ([_G, _PP, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _D, _D, _P, _S, _P], ctypes.c_int),
     "cosmos_evolve_host": ([_G, _PP, _P, _P, _P, ctypes.c_int, _D, _D, _P, _S, _P], ctypes.c_int),
+    "cosmos_evolve_host_many": ([_G, _PP, ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_int, _D, _D, _P, _S, _P],
+                                ctypes.c_int),
     "cosmos_constraints": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P, _S, _P], ctypes.c_int),
     "cosmos_constraints_noalloc": ([_G, _PP, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "cosmos_checkpoint_save": ([ctypes.c_char_p, _G, _PP, _P, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, _P],
@@ -237,6 +239,19 @@ def cosmos_evolve_host(g, p, host_in, host_out, dev_state, steps, t, dt, ws=None
     w, nb = _ws(ws)
     return lib().cosmos_evolve_host(ctypes.byref(g), ctypes.byref(p), _ptr(host_in), _ptr(host_out),
                                     _ptr(dev_state), int(steps), float(t), float(dt), w, nb, _stream(stream))
+
+
+def cosmos_evolve_host_many(g, p, host_in, host_out, dev_states, steps, t, dt, ws=None, stream=None) -> int:
+    """host_in, host_out: sequences of host tensors (one per state); dev_states: device buffers."""
+    n = len(host_in)
+    if len(host_out) != n:
+        return COSMOS_EINVAL
+    ins = (ctypes.c_void_p * max(n, 1))(*[_ptr(x) for x in host_in])
+    outs = (ctypes.c_void_p * max(n, 1))(*[_ptr(x) for x in host_out])
+    devs = (ctypes.c_void_p * max(len(dev_states), 1))(*[_ptr(x) for x in dev_states])
+    w, nb = _ws(ws)
+    return lib().cosmos_evolve_host_many(ctypes.byref(g), ctypes.byref(p), n, ins, outs, devs, len(dev_states),
+                                         int(steps), float(t), float(dt), w, nb, _stream(stream))
 
 
 def cosmos_constraints(g, p, state, ham_mom, norms_out, ws=None, stream=None) -> int:

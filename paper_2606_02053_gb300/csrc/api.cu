@@ -553,20 +553,15 @@ int cosmos_stage_pass(const cosmos_grid* g, const cosmos_params* p, int pass, in
                    (double*)ws, L, (cudaStream_t)stream, 1 << pass, 0, 0, 0, 0, nullptr, expo_flags);
 }
 
-int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
-                    size_t ws_bytes, void* stream) {
-  int e = validate(g, p);
-  if (e) return e;
-  if (!state) return COSMOS_EINVAL;
-  if (!aligned16(state)) return COSMOS_EALIGN;
-  const WsLayout L = ws_layout(g, p, COSMOS_OP_RK4);
-  if ((e = check_ws(L, ws, ws_bytes))) return e;
-  double* w = (double*)ws;
+namespace {
+// One RK4 step of `state` in place on stream s (arguments already checked).
+int rk4_on(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, double* w,
+           const WsLayout& L, cudaStream_t s) {
   double* A = w + L.stageA;
   double* B = w + L.stageB;
   double* acc = w + L.acc;
-  cudaStream_t s = (cudaStream_t)stream;
   const double dt2 = 0.5 * dt;
+  int e;
   // stage 1 scans U_n (the caller may have changed it); each algebra pass records the
   // exponents of the state it writes, so stages 2-4 need no scan
   if ((e = run_stage(g, p, MODE_S1, state, state, A, acc, t, dt2, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 6))) return e;
@@ -575,6 +570,18 @@ int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state,
   if ((e = run_stage(g, p, MODE_S23, B, state, A, acc, t + dt2, dt, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 3)))
     return e;
   return run_stage(g, p, MODE_S4, A, state, nullptr, acc, t + dt, dt / 6.0, 2.0, w, L, s, 7, 0, 0, 0, 0, nullptr, 1);
+}
+}  // namespace
+
+int cosmos_rk4_step(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt, void* ws,
+                    size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (!state) return COSMOS_EINVAL;
+  if (!aligned16(state)) return COSMOS_EALIGN;
+  const WsLayout L = ws_layout(g, p, COSMOS_OP_RK4);
+  if ((e = check_ws(L, ws, ws_bytes))) return e;
+  return rk4_on(g, p, state, t, dt, (double*)ws, L, (cudaStream_t)stream);
 }
 
 int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double* state, double t, double dt,
@@ -700,6 +707,101 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
     }
   }
   CK(cudaStreamSynchronize(hp.cs));
+  CK(cudaStreamSynchronize(s));
+  return COSMOS_OK;
+}
+
+namespace {
+constexpr int MANY_MAX_BUF = 16;
+// Streams and per-buffer events of cosmos_evolve_host_many.
+struct ManyPipeline {
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, ev_in[MANY_MAX_BUF] = {}, ev_comp[MANY_MAX_BUF] = {}, ev_out[MANY_MAX_BUF] = {};
+  ~ManyPipeline() {
+    for (int b = 0; b < MANY_MAX_BUF; ++b)
+      for (cudaEvent_t e : {ev_in[b], ev_comp[b], ev_out[b]})
+        if (e) cudaEventDestroy(e);
+    if (start) cudaEventDestroy(start);
+    if (in) cudaStreamDestroy(in);
+    if (out) cudaStreamDestroy(out);
+  }
+};
+
+bool ranges_overlap(const void* a, const void* b, size_t bytes) {
+  const char *x = (const char*)a, *y = (const char*)b;
+  return x < y + bytes && y < x + bytes;
+}
+}  // namespace
+
+int cosmos_evolve_host_many(const cosmos_grid* g, const cosmos_params* p, int count, const double* const* host_in,
+                            double* const* host_out, double* const* dev_states, int nbuf, int steps, double t,
+                            double dt, void* ws, size_t ws_bytes, void* stream) {
+  int e = validate(g, p);
+  if (e) return e;
+  if (count < 0 || steps < 0 || nbuf < 1 || nbuf > MANY_MAX_BUF) return COSMOS_EINVAL;
+  if (count == 0) return COSMOS_OK;
+  if (!host_in || !host_out || !dev_states) return COSMOS_EINVAL;
+  const size_t fs = cosmos_field_stride(g);
+  const int nf = cosmos_nfields(p);
+  const size_t bytes = fs * (size_t)nf * sizeof(double);
+  for (int b = 0; b < nbuf; ++b) {
+    if (!dev_states[b]) return COSMOS_EINVAL;
+    if (!aligned16(dev_states[b])) return COSMOS_EALIGN;
+    for (int c = 0; c < b; ++c)
+      if (ranges_overlap(dev_states[b], dev_states[c], bytes)) return COSMOS_EINVAL;
+  }
+  // a result must not land on inputs that later copies still read
+  for (int i = 0; i < count; ++i) {
+    if (!host_in[i] || !host_out[i]) return COSMOS_EINVAL;
+    for (int j = 0; j < count; ++j)
+      if (ranges_overlap(host_out[i], host_in[j], bytes)) return COSMOS_EINVAL;
+  }
+  WsLayout L{};
+  if (steps > 0) {
+    L = ws_layout(g, p, COSMOS_OP_RK4);
+    if ((e = check_ws(L, ws, ws_bytes))) return e;
+  }
+  double* w = (double*)ws;
+  cudaStream_t s = (cudaStream_t)stream;
+  // State i lives in dev_states[i % nbuf].  The copy-in stream fills a buffer
+  // once the copy-out stream has emptied it; the state is advanced on `s`;
+  // the copy-out stream reads it back.  Copies of other states overlap each
+  // computation, and copies in and out overlap each other.
+  ManyPipeline mp;
+  CK(cudaStreamCreateWithFlags(&mp.in, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&mp.out, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&mp.start, cudaEventDisableTiming));
+  for (int b = 0; b < nbuf; ++b) {
+    CK(cudaEventCreateWithFlags(&mp.ev_in[b], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&mp.ev_comp[b], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&mp.ev_out[b], cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(mp.start, s));  // earlier work on `s` may still use the buffers
+  CK(cudaStreamWaitEvent(mp.in, mp.start, 0));
+  CK(cudaStreamWaitEvent(mp.out, mp.start, 0));
+  for (int i = 0; i < count && i < nbuf; ++i) {
+    CK(cudaMemcpyAsync(dev_states[i], host_in[i], bytes, cudaMemcpyHostToDevice, mp.in));
+    CK(cudaEventRecord(mp.ev_in[i], mp.in));
+  }
+  for (int i = 0; i < count; ++i) {
+    const int b = i % nbuf;
+    double* d = dev_states[b];
+    CK(cudaStreamWaitEvent(s, mp.ev_in[b], 0));
+    for (int k = 0; k < steps; ++k)
+      if ((e = rk4_on(g, p, d, t + k * dt, dt, w, L, s))) return e;
+    CK(cudaEventRecord(mp.ev_comp[b], s));
+    CK(cudaStreamWaitEvent(mp.out, mp.ev_comp[b], 0));
+    CK(cudaMemcpyAsync(host_out[i], d, bytes, cudaMemcpyDeviceToHost, mp.out));
+    CK(cudaEventRecord(mp.ev_out[b], mp.out));
+    const int j = i + nbuf;  // the next state for this buffer
+    if (j < count) {
+      CK(cudaStreamWaitEvent(mp.in, mp.ev_out[b], 0));
+      CK(cudaMemcpyAsync(d, host_in[j], bytes, cudaMemcpyHostToDevice, mp.in));
+      CK(cudaEventRecord(mp.ev_in[b], mp.in));
+    }
+  }
+  CK(cudaStreamSynchronize(mp.in));
+  CK(cudaStreamSynchronize(mp.out));
   CK(cudaStreamSynchronize(s));
   return COSMOS_OK;
 }

@@ -191,3 +191,40 @@ def test_fmr_hierarchy_validation_without_gpu(libpath):
     states = (ctypes.c_void_p * 3)(256, 512, 768)
     assert C.lib().cosmos_fmr_step(ctypes.byref(good), ctypes.byref(p), states, 0.0, 0.1, ctypes.c_void_p(256),
                                    nb - 8, None) == C.COSMOS_EWORKSPACE
+
+
+def test_pipelined_host_evolution_refuses_bad_arguments_before_any_copy(libpath):
+    """cosmos_evolve_host_many checks its buffers before it creates a stream or
+    copies anything: a negative count or step count, nbuf outside 1..16, a NULL
+    buffer, two device buffers that overlap, and a result buffer that overlaps an
+    input buffer are refused; count = 0 does nothing.  The addresses are never
+    dereferenced."""
+    from paper_2606_02053_gb300 import cosmos as C
+
+    g = C.make_grid((16, 8, 8), 0.05)
+    p = C.make_params()
+    bytes_ = C.cosmos_field_stride(g) * C.cosmos_nfields(p) * 8
+    base = 1 << 20
+
+    def arr(*xs):
+        return (ctypes.c_void_p * max(len(xs), 1))(*xs)
+
+    def call(count, ins, outs, devs, nbuf, steps=1, ws=None):
+        return C.lib().cosmos_evolve_host_many(ctypes.byref(g), ctypes.byref(p), count, ins, outs, devs, nbuf, steps,
+                                               0.0, 0.01, ws, 0, None)
+
+    ins, outs = arr(base), arr(base + 4 * bytes_)
+    devs = arr(base + 8 * bytes_, base + 10 * bytes_)
+    assert call(0, None, None, None, 1) == C.COSMOS_OK
+    assert call(-1, ins, outs, devs, 2) == C.COSMOS_EINVAL
+    assert call(1, ins, outs, devs, 2, steps=-1) == C.COSMOS_EINVAL
+    for nbuf in (0, 17):
+        assert call(1, ins, outs, devs, nbuf) == C.COSMOS_EINVAL
+    assert call(1, ins, arr(None), devs, 2) == C.COSMOS_EINVAL
+    assert call(1, ins, outs, arr(base + 8 * bytes_, base + 8 * bytes_ + 256), 2) == C.COSMOS_EINVAL
+    assert call(1, ins, arr(base + bytes_ // 2), devs, 2) == C.COSMOS_EINVAL  # result over the input
+    assert call(2, arr(base, base + 2 * bytes_), arr(base + 4 * bytes_, base + 2 * bytes_ + 8), devs,
+                2) == C.COSMOS_EINVAL  # a result over a later input
+    assert call(1, ins, outs, arr(base + 8 * bytes_ + 8), 1) == C.COSMOS_EALIGN
+    # with valid buffers the workspace check comes next, still before any copy
+    assert call(1, ins, outs, devs, 2, ws=ctypes.c_void_p(base + 16 * bytes_)) == C.COSMOS_EWORKSPACE

@@ -304,6 +304,47 @@ def test_evolve_host_matches_device_steps(C, fluid, scalar, n, pitch):
             assert torch.equal(dev, ev.state), (steps, pinned)
 
 
+@pytest.mark.parametrize("fluid,scalar,n,pitch", [(0, 0, (37, 13, 11), 40), (1, 1, (20, 12, 5), None)])
+def test_pipelined_host_evolution_of_many_states_matches_device_steps(C, fluid, scalar, n, pitch):
+    """cosmos_evolve_host_many: five different states (one of them given twice),
+    each evolved from host memory through 1, 2 or 3 device buffers, equal bitwise
+    to cosmos_rk4_step on the device; pinned and pageable host buffers; a result
+    over an input buffer is refused."""
+    from paper_2606_02053_gb300 import inputs
+    from paper_2606_02053_gb300.evolve import Evolution
+
+    h = 1.0 / n[0]
+    p = C.make_params(fluid=fluid, scalar=scalar, H0=2.0 * fluid)
+    g = C.make_grid(n, h, pitch=pitch)
+    ev = Evolution(g, p)
+    states = []
+    for q in range(4):
+        ev.set_state(inputs.smooth_state(n, seed=90 + q + 10 * fluid, fluid=fluid, scalar=scalar, scale=0.5))
+        states.append(ev.state.clone())
+    states.append(states[1])  # the same inputs again
+    dt = 0.25 * h
+    want = {}
+    for steps in (0, 1, 2):
+        for q in range(4):
+            ev.state.copy_(states[q])
+            ev.step(0.01, dt, steps=steps)
+            want[steps, q] = ev.state.cpu()
+    for steps in (1, 2, 0):
+        for nbuf in (1, 2, 3):
+            for pinned in (True, False):
+                ins = [x.cpu().pin_memory() if pinned else x.cpu() for x in states]
+                outs = [torch.full_like(ins[0], float("nan")) for _ in states]
+                if pinned:
+                    outs = [o.pin_memory() for o in outs]
+                devs = [torch.empty_like(states[0]) for _ in range(nbuf)]
+                C.check(C.cosmos_evolve_host_many(g, p, ins, outs, devs, steps, 0.01, dt, ev.ws_rk4))
+                for i, o in enumerate(outs):
+                    assert torch.equal(o, want[steps, i if i < 4 else 1]), (steps, nbuf, pinned, i)
+    ins = [states[0].cpu().pin_memory(), states[1].cpu().pin_memory()]
+    devs = [torch.empty_like(states[0]) for _ in range(2)]
+    assert C.cosmos_evolve_host_many(g, p, ins, [ins[1], ins[0]], devs, 1, 0.0, dt, ev.ws_rk4) == C.COSMOS_EINVAL
+
+
 def test_isocurvature_init_and_evolution_parity(C, O):
     """FLRW + zeta + massless-scalar isocurvature data (id kind 2) and 20 RK4
     steps of the fluid + scalar system against the oracle."""
