@@ -6,6 +6,7 @@ from __future__ import annotations
 
 import argparse
 import os
+import pathlib
 import sys
 
 from . import bssn
@@ -138,7 +139,7 @@ def main(argv=None):
     stale = []
     for fn, text in files.items():
         path = os.path.join(OUT_DIR, fn)
-        old = open(path).read() if os.path.exists(path) else None
+        old = pathlib.Path(path).read_text() if os.path.exists(path) else None
         if old != text:
             stale.append(fn)
             if not a.check:

@@ -4,6 +4,7 @@ No compute calls (no GPU needed)."""
 import ctypes
 import glob
 import os
+import pathlib
 import re
 import subprocess
 
@@ -15,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
-        text = open(h).read()
+        text = pathlib.Path(h).read_text()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"\b(cosmos_[a-z0-9_]+)\s*\(", text):
             names.add(m.group(1))

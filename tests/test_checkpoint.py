@@ -10,6 +10,7 @@ GPU needed, the same file code as for device buffers (tests/test_gpu_checkpoint.
 """
 import json
 import os
+import pathlib
 
 import numpy as np
 import pytest
@@ -88,11 +89,11 @@ def test_mismatch_and_corruption_are_refused(lib, tmp_path):
     refused(g, p, str(tmp_path / "missing.bin"), C.COSMOS_EIO)
     assert C.cosmos_checkpoint_load(path, C.make_grid((10, 6, 5), 0.1, pitch=16), p,
                                     np.zeros((28, 5, 6, 16)))[0] == C.COSMOS_OK  # another pitch is fine
-    raw = open(path, "rb").read()
+    raw = pathlib.Path(path).read_bytes()
     for name, data in (("flip", raw[:5000] + bytes([raw[5000] ^ 1]) + raw[5001:]),
                        ("short", raw[:-8]), ("long", raw + b"\0" * 8), ("header", raw[:100])):
         bad = str(tmp_path / f"{name}.bin")
-        open(bad, "wb").write(data)
+        pathlib.Path(bad).write_bytes(data)
         refused(g, p, bad)
 
 

@@ -13,6 +13,7 @@ and compare them with the expression graph's own interpreter:
   rounding of the reordered sums.
 """
 import math
+import pathlib
 import re
 
 import numpy as np
@@ -109,7 +110,7 @@ def vac_rhs_body():
 
     path = os.path.join(os.path.dirname(__file__), "..", "paper_2606_02053_gb300", "csrc", "generated",
                         "bssn_algebra.cuh")
-    src = open(path).read()
+    src = pathlib.Path(path).read_text()
     ns = src[src.index("namespace alg_vac {"):src.index("}  // namespace alg_vac")]
     start = ns.index("void rhs(const In& in, Out&& out, const AlgebraParams& p) {")
     end = ns.index("\n}\n", start)

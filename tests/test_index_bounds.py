@@ -7,6 +7,7 @@ neighbour offsets (i + o, j + o, k + o, |o| <= 3, for every thread of a tile
 that starts inside the grid) and the staging of the D_y / D_z sums (x in
 i0 - 2 .. i0 + BX + 1, rows j0 - 2 .. j0 + DBY + 1, planes k - 2 .. k + 2)."""
 import os
+import pathlib
 import re
 
 import numpy as np
@@ -16,7 +17,7 @@ COMMON = os.path.join(os.path.dirname(HERE), "paper_2606_02053_gb300", "csrc", "
 
 
 def constants():
-    src = open(COMMON).read()
+    src = pathlib.Path(COMMON).read_text()
     bx = int(re.search(r"constexpr int BX = (\d+);", src).group(1))
     dby = int(re.search(r"#define COSMOS_DERIV_ROWS (\d+)", src).group(1))
     m = re.search(r"near_indices\(const DevGrid& g\) \{ return g\.nx >= BX \+ (\d+) && g\.ny >= DBY \+ (\d+) "
