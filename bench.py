@@ -49,16 +49,18 @@ COMBINE_FLOPS = [2, 4, 4, 3]
 # the algebra pass: the mean over a step's stages 1, 2, 3, 4), and the hash of
 # the kernel sources it was taken on.  Reported scaled to the bench grid by
 # points; null when the kernel sources differ from the profiled ones.
-NCU_TRAFFIC = {"sources_sha256_16": "8db15fd6f6a7d713", "grid": 96,
+NCU_TRAFFIC = {"sources_sha256_16": "d9458dbd967c761b", "grid": 96,
                "bytes_per_launch": {
                    # exponent scan (stage 1 only) + limb copy + integer pass, mean over the 4 stages of a step
-                   "derivative": ((169878016 + 3215872) + (169889792 + 122542080) + (237255680 + 1092109056)
-                                  + (169890304 + 122353152) + (237198080 + 1092582400)
-                                  + (169882624 + 121916160) + (237166592 + 1092224000)
-                                  + (169893120 + 122293504) + (237318656 + 1092241152)) / 4,
+                   "derivative": ((169876480 + 2942720) + (169888256 + 122609664) + (237270784 + 1092062720)
+                                  + (169886464 + 122411776) + (237136384 + 1092135680)
+                                  + (169885440 + 122008576) + (237230592 + 1092202752)
+                                  + (169884160 + 122150144) + (237212672 + 1092190720)) / 4,
                    # algebra pass, modes 1, 2, 2, 3 of one step
-                   "algebra": ((1382648576 + 493276672) + (1673435136 + 457987840) + (1675968256 + 458668544)
-                               + (1659180288 + 432637952)) / 4}}
+                   "algebra": ((1382906368 + 493360640)
+                               + (1673651456 + 457847040)
+                               + (1675347712 + 457922048)
+                               + (1659218176 + 432763648)) / 4}}
 # derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
 DERIV_DOUBLES = 162
 KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_int.cuh", "limbs.cu", "stage_vac.cu",
