@@ -160,12 +160,13 @@ def algebra(fluid: bool, scalar: bool):
     for i in range(3):
         Ci = [[gu[m, 0] * Gu[k][0, i] + gu[m, 1] * Gu[k][1, i] + gu[m, 2] * Gu[k][2, i] for m in range(3)]
               for k in range(3)]
+        # Gamma_jkm is symmetric in k, m: T_ij sums (C[k][m][i] + C[m][k][i]) Gamma_jkm over k <= m
+        Cs = {(k, m): (Ci[k][m] if k == m else Ci[k][m] + Ci[m][k]) for (k, m) in PAIRS}
         for j in range(3):
             s = None
-            for k in range(3):
-                for m in range(3):
-                    t = Ci[k][m] * Gl[j][k, m]
-                    s = t if s is None else s + t
+            for (k, m) in PAIRS:
+                t = Cs[(k, m)] * Gl[j][k, m]
+                s = t if s is None else s + t
             add_to(PIDX[(i, j)], 2.0 * s if i == j else s)  # T_ij into R_ij (T_ii counted twice)
             if j >= i:
                 u_ = None
@@ -175,21 +176,27 @@ def algebra(fluid: bool, scalar: bool):
                         u_ = t if u_ is None else u_ + t
                 add_to(PIDX[(i, j)], u_)  # U_ij
     Gd = [contract_sym(gu2, Gu[k]) for k in range(3)]
-    def V(i, j):  # gt_ki d_j Gt^k + Gd^k Gamma_ijk
-        s = None
-        for k in range(3):
-            t = gt[k, i] * dGt(j, k) + Gd[k] * Gl[i][j, k]
-            s = t if s is None else s + t
-        return s
-
+    # R_ij as one flat sum, the constant factors folded into factors formed once:
+    #   -1/2 gt^lm d_l d_m gt_ij          -> (-1/2 gt^lm) d_l d_m gt_ij
+    #   gt_k(i d_j) Gt^k                   -> (1/2 gt_ki) d_j Gt^k + (1/2 gt_kj) d_i Gt^k (i != j)
+    #   Gd^k Gamma_(ij)k = 1/2 Gd^k d_k gt_ij   (Gamma_ijk + Gamma_jik = d_k gt_ij)
+    ngu2 = [-0.5 * x for x in gu2]
+    hGd = [0.5 * x for x in Gd]
+    hgt = Sym([0.5 * x for x in gt.c])
     Ric = []
     for m, (i, j) in enumerate(PAIRS):
-        lap = None
+        r = None
         for q, (l, n) in enumerate(PAIRS):
-            t = gu2[q] * ddgt(l, n, i, j)
-            lap = t if lap is None else lap + t
-        sym_v = V(i, i) if i == j else 0.5 * (V(i, j) + V(j, i))
-        Ric.append(-0.5 * lap + sym_v + acc[m])
+            t = ngu2[q] * ddgt(l, n, i, j)
+            r = t if r is None else r + t
+        for k in range(3):
+            if i == j:
+                r = r + gt[k, i] * dGt(i, k)
+            else:
+                r = r + hgt[k, i] * dGt(j, k) + hgt[k, j] * dGt(i, k)
+        for k in range(3):
+            r = r + hGd[k] * dgt(k, i, j)
+        Ric.append(r + acc[m])
     # the remaining uses of the second-kind Christoffels, formed here so that
     # those 18 values die early
     Gu_dchi = [Gu[0][i, j] * dchi[0] + Gu[1][i, j] * dchi[1] + Gu[2][i, j] * dchi[2] for (i, j) in PAIRS]
