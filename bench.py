@@ -49,18 +49,18 @@ COMBINE_FLOPS = [2, 4, 4, 3]
 # the algebra pass: the mean over a step's stages 1, 2, 3, 4), and the hash of
 # the kernel sources it was taken on.  Reported scaled to the bench grid by
 # points; null when the kernel sources differ from the profiled ones.
-NCU_TRAFFIC = {"sources_sha256_16": "d9458dbd967c761b", "grid": 96,
+NCU_TRAFFIC = {"sources_sha256_16": "6129913db8cd4ae6", "grid": 96,
                "bytes_per_launch": {
                    # exponent scan (stage 1 only) + limb copy + integer pass, mean over the 4 stages of a step
-                   "derivative": ((169876480 + 2942720) + (169888256 + 122609664) + (237270784 + 1092062720)
-                                  + (169886464 + 122411776) + (237136384 + 1092135680)
-                                  + (169885440 + 122008576) + (237230592 + 1092202752)
-                                  + (169884160 + 122150144) + (237212672 + 1092190720)) / 4,
+                   "derivative": ((169877760 + 3258880) + (169882880 + 122540544) + (237195264 + 1092143360)
+                                  + (169875712 + 122436608) + (237027584 + 1092392960)
+                                  + (169882112 + 121968384) + (237173760 + 1092693760)
+                                  + (169882880 + 122204928) + (237097728 + 1092242688)) / 4,
                    # algebra pass, modes 1, 2, 2, 3 of one step
-                   "algebra": ((1382906368 + 493360640)
-                               + (1673651456 + 457847040)
-                               + (1675347712 + 457922048)
-                               + (1659218176 + 432763648)) / 4}}
+                   "algebra": ((1396294400 + 521755648)
+                               + (1671427584 + 385866240)
+                               + (1672915200 + 386181120)
+                               + (1646590720 + 483951104)) / 4}}
 # derivative-pass buffer: first + second derivatives and KO terms per point (vacuum)
 DERIV_DOUBLES = 162
 KERNEL_SOURCES = ["common.cuh", "stage_kernel.cuh", "stage_int.cuh", "limbs.cu", "stage_vac.cu",
