@@ -266,8 +266,9 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
                        double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
 /* End-to-end steps of `count` independent states with HOST buffers, pipelined
- * (the paper's evolution applied to a sequence of grids, e.g. the states of a
- * parameter scan kept in host memory): state i is copied from host_in[i] to
+ * (the RK4 evolution of section "Physical system settings", as cosmos_rk4_step,
+ * applied to a sequence of grids, e.g. the states of a parameter scan kept in
+ * host memory): state i is copied from host_in[i] to
  * a device buffer, advanced `steps` RK4 steps from time t, and copied back to
  * host_out[i]; every result is bitwise that of cosmos_rk4_step applied
  * `steps` times (and of cosmos_evolve_host).  State i lives in
