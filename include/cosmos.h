@@ -261,7 +261,8 @@ int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double*
  * device-to-host copy in up to eight slabs of z-planes, each started when the
  * last algebra pass has written them.  The result is bitwise that of
  * cosmos_rk4_step.  Errors: COSMOS_EINVAL (NULL buffer, steps < 0),
- * COSMOS_EALIGN, COSMOS_EWORKSPACE, COSMOS_ECUDA. */
+ * COSMOS_EALIGN, COSMOS_EWORKSPACE, COSMOS_ECUDA (the call returns only after
+ * its own copies have ended, on errors too). */
 int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const double* host_in, double* host_out,
                        double* dev_state, int steps, double t, double dt, void* ws, size_t ws_bytes, void* stream);
 
@@ -285,7 +286,7 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
  * every result is in host memory.  Errors: COSMOS_EINVAL (count or steps < 0,
  * nbuf out of range, a NULL or overlapping buffer), COSMOS_EALIGN,
  * COSMOS_EWORKSPACE, COSMOS_ECUDA (then the contents of the buffers are
- * undefined). */
+ * undefined; the call still returns only after its own copies have ended). */
 int cosmos_evolve_host_many(const cosmos_grid* g, const cosmos_params* p, int count, const double* const* host_in,
                             double* const* host_out, double* const* dev_states, int nbuf, int steps, double t,
                             double dt, void* ws, size_t ws_bytes, void* stream);

@@ -609,10 +609,14 @@ int cosmos_rk4_step_stages(const cosmos_grid* g, const cosmos_params* p, double*
 namespace {
 // Copy stream and events of one cosmos_evolve_host call; destroyed on every
 // return path (work still queued on them completes first).
+// Copy stream and events of cosmos_evolve_host.  On every return, an early
+// error return included, the copy stream is waited for first: no copy of the
+// call writes the caller's host buffer after the call has returned.
 struct HostPipeline {
   cudaStream_t cs = nullptr;
   cudaEvent_t ev[16] = {};
   ~HostPipeline() {
+    if (cs) cudaStreamSynchronize(cs);
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);
     if (cs) cudaStreamDestroy(cs);
@@ -713,11 +717,14 @@ int cosmos_evolve_host(const cosmos_grid* g, const cosmos_params* p, const doubl
 
 namespace {
 constexpr int MANY_MAX_BUF = 16;
-// Streams and per-buffer events of cosmos_evolve_host_many.
+// Streams and per-buffer events of cosmos_evolve_host_many.  As for
+// HostPipeline, the copy streams are waited for on every return.
 struct ManyPipeline {
   cudaStream_t in = nullptr, out = nullptr;
   cudaEvent_t start = nullptr, ev_in[MANY_MAX_BUF] = {}, ev_comp[MANY_MAX_BUF] = {}, ev_out[MANY_MAX_BUF] = {};
   ~ManyPipeline() {
+    if (in) cudaStreamSynchronize(in);
+    if (out) cudaStreamSynchronize(out);
     for (int b = 0; b < MANY_MAX_BUF; ++b)
       for (cudaEvent_t e : {ev_in[b], ev_comp[b], ev_out[b]})
         if (e) cudaEventDestroy(e);
