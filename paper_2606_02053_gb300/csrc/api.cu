@@ -888,18 +888,22 @@ int cosmos_probe_fp64(double* scratch, double* flops_out, void* stream) {
   if (sms > 152) sms = 152;  // scratch holds 152 * 8 * 256 doubles
   cudaStream_t s = (cudaStream_t)stream;
   const int blocks = sms * 8, threads = 256, iters = 4096;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  struct Events {  // destroyed on every return
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Events() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } ev;
+  CK(cudaEventCreate(&ev.e0));
+  CK(cudaEventCreate(&ev.e1));
   fp64_fma_chains<<<blocks, threads, 0, s>>>(scratch, iters, 0.999999, 1e-7);  // warm-up
-  CK(cudaEventRecord(e0, s));
+  CK(cudaEventRecord(ev.e0, s));
   fp64_fma_chains<<<blocks, threads, 0, s>>>(scratch, iters, 0.999999, 1e-7);
-  CK(cudaEventRecord(e1, s));
-  CK(cudaEventSynchronize(e1));
+  CK(cudaEventRecord(ev.e1, s));
+  CK(cudaEventSynchronize(ev.e1));
   float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  CK(cudaEventElapsedTime(&ms, ev.e0, ev.e1));
   *flops_out = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
   return COSMOS_OK;
 }

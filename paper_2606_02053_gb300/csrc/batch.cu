@@ -370,7 +370,11 @@ int cosmos_batch_time_stage(cosmos_batch b, int reps, double* ms_out, void* stre
                                          : (b->p.scalar ? launch_batch_stage_scalar : launch_batch_stage_vac);
   const dim3 grid(b->sms * b->tune.blocks_per_sm), block(b->tune.block_x, b->tune.block_y);
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return COSMOS_ECUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess) return COSMOS_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return COSMOS_ECUDA;
+  }
   int rc = COSMOS_OK;
   for (int r = -1; r < reps && rc == COSMOS_OK; ++r) {  // r = -1: warm-up
     if (r == 0) cudaEventRecord(e0, s);
