@@ -19,14 +19,12 @@ rank evolves its own 256^3 instance (independent replicas, weak scaling); with
 from __future__ import annotations
 
 import argparse
-import ctypes
 import json
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))

@@ -1,5 +1,4 @@
 """Reverse mode on the GPU against the oracle's tape and against finite differences."""
-import ctypes
 
 import numpy as np
 import pytest

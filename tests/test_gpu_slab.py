@@ -5,7 +5,6 @@ whole grid -- bitwise, for vacuum, fluid + scalar and FLRW + zeta data, on
 uneven slabs and a padded row pitch.  The same code with DistExchange runs one
 slab per GPU; its exchange is checked on CPU ranks in test_slab_gloo.py.
 """
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

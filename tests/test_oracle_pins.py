@@ -2,7 +2,6 @@
 
 Each test names the property it pins and the mistake it would catch.
 """
-import math
 
 import numpy as np
 import pytest
